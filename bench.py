@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Throughput of the fused LB stream-collide path on GB300: MLUPS and fraction
+of the HBM roofline for FP32 storage (FP16/BF16 storage beside it), with the
+Lorenz-Mie error of the far-field intensity it produces.
+
+Workload: the 384^3 dielectric sphere (n = 1.33, x = 5, lambda = 30 cells,
+x-polarised plane wave along +z, 16-cell absorbing layer).  One bench step is
+one pass of the whole hot path: one DFT window of T = 3 lambda = 90 lattice
+updates (pull streaming with the Eq. 4 boundary, TF/SF source, moments,
+running FP64 DFT on the NTFF box, collision, absorbing layer) followed by the
+FP64 near-to-far-field projection to |S(theta, phi)|^2 at 181 x 3 angles.
+The default 3 warm-up + 27 timed steps run the 30 periods of the workload, so
+the last step's |S|^2 is the steady-state result compared with Mie.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbem|reference]
+
+N > 1 (launched under torchrun): independent replicas, one problem per GPU.
+--impl reference times the FP64 CPU oracle on a bounded slab of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+PROFILES = os.path.join(ROOT, "profiles")
+METRIC = "MLUPS and % of HBM roofline at 1 GB300 (FP32 vs FP16 storage) at stated Mie error"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def b_cell(mode: str, storage: str) -> int:
+    q = 42 if mode == "3d" else 21
+    s = 4 if storage == "f32" else 2
+    return 2 * q * s + 4
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("step.cu", "lbem_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2510_11042_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(workload: str, storage: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    path = os.path.join(PROFILES, "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d[workload][storage]
+        if e.get("kernel_hash") != kernel_source_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def mie_reference():
+    d = np.loadtxt(os.path.join(GOLDEN, "mie_sphere_x5_m1.33.txt"))
+    return d[:, 1:4]  # [181][phi = 0, 45, 90]
+
+
+def nrms(s, ref):
+    """Eq. 13: RMS of the difference over the angles / max of the reference."""
+    return float(np.sqrt(np.mean((s - ref) ** 2)) / np.max(ref))
+
+
+def angles():
+    th = np.radians(np.arange(181.0))
+    return (np.concatenate([th, th, th]),
+            np.concatenate([np.zeros(181), np.full(181, math.pi / 4), np.full(181, math.pi / 2)]))
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2510_11042_gb300 import build as lib_build
+    from paper_2510_11042_gb300 import lbem
+
+    if rank == 0:
+        lib_build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    lbem.lib()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    prob = W.sphere_problem(n=args.size)
+    nx, ny, nz = prob.shape
+    cells = nx * ny * nz
+    T = prob.period
+    theta, phi = angles()
+    ref = mie_reference()
+    results = {}
+
+    def one_storage(storage, K, Wm, timed_main):
+        solver = lbem.Solver(prob.shape, prob.eps, "3d", storage, prob.absorber_width,
+                             prob.sigma_max, device=dev)
+        solver.inject(prob.wave)
+        h = solver.h
+        stream = solver.stream
+
+        def bench_step(ev_pair=None):
+            lbem.lbem_set_dft_window(h, solver.time + 1, 1)
+            if ev_pair:
+                ev_pair[0].record(stream)
+            lbem.lbem_step(h, T)
+            if ev_pair:
+                ev_pair[1].record(stream)
+            return lbem.lbem_far_field(h, theta, phi)
+
+        for _ in range(Wm):
+            bench_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local_rank) if timed_main else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        launches0 = lbem.lbem_kernel_launches(h)
+        torch.cuda.synchronize(dev)
+        barrier()
+        start.record(stream)
+        s2 = None
+        for k in range(K):
+            s2 = bench_step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = lbem.lbem_kernel_launches(h) - launches0
+        total_ms = start.elapsed_time(end)
+        step_kernel_ms = sum(a.elapsed_time(b) for a, b in evs) / (K * T)
+        s2 = s2.reshape(3, 181).T
+        out = dict(total_ms=total_ms, ms_per_step=total_ms / K, kernel_ms=step_kernel_ms,
+                   launches=launches, clocks=clocks, periods=solver.time // T,
+                   mie_nrms=[nrms(s2[:, j], ref[:, j]) for j in range(3)],
+                   incident=lbem.lbem_incident_amplitude(h))
+        # end-to-end: host (pinned) permittivity in, |S|^2 out, through the C ABI
+        if timed_main:
+            eps_host = torch.from_numpy(prob.eps).pin_memory()
+            E = min(K, 3)
+            torch.cuda.synchronize(dev)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(E):
+                lbem.lbem_set_permittivity(h, eps_host)
+                bench_step()          # ends with the |S|^2 copy to the host
+            torch.cuda.synchronize(dev)
+            barrier()
+            t_e2e = (time.perf_counter() - t0) / E
+            out["e2e_s_per_step"] = t_e2e
+            out["h2d_bytes"] = int(prob.eps.nbytes + theta.nbytes + phi.nbytes)
+            out["d2h_bytes"] = int(theta.size * 8)
+        solver.close()
+        del solver
+        torch.cuda.empty_cache()
+        return out
+
+    K, Wm = args.steps, args.warmup
+    main = one_storage("f32", K, Wm, True)
+    secondary = {}
+    if not args.fp32_only:
+        for st in ("f16", "bf16"):
+            secondary[st] = one_storage(st, K, Wm, False)
+
+    # max over ranks of the timed region
+    t_main = main["total_ms"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_main], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_main = float(t.item())
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    ups = cells * T * K * world
+    value = ups / (t_main / 1e3) / 1e6
+    bc = b_cell("3d", "f32")
+    achieved = bc * cells / (main["kernel_ms"] / 1e3) / 1e9
+    traffic = traffic_from_profile(f"sphere_{args.size}", "f32")
+    e2e_val = cells * T / main["e2e_s_per_step"] / 1e6 * world
+    storage_modes = {"f32": {"mlups": round(value / world, 1),
+                             "kernel_ms": round(main["kernel_ms"], 4),
+                             "hbm_frac": round(achieved / hbm, 4),
+                             "mie_nrms_phi_0_45_90": [round(v, 5) for v in main["mie_nrms"]]}}
+    for st, r in secondary.items():
+        bcs = b_cell("3d", st)
+        ach = bcs * cells / (r["kernel_ms"] / 1e3) / 1e9
+        storage_modes[st] = {"mlups": round(cells * T * K / (r["total_ms"] / 1e3) / 1e6, 1),
+                             "kernel_ms": round(r["kernel_ms"], 4),
+                             "hbm_frac": round(ach / hbm, 4),
+                             "speedup_vs_f32": round(main["kernel_ms"] / r["kernel_ms"], 3),
+                             "mie_nrms_phi_0_45_90": [round(v, 5) for v in r["mie_nrms"]]}
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": round(t_main / K, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"sphere_{args.size}^3_n1.33_x5_lambda30_W16_fp32_storage",
+                   "cells": cells, "lattice_updates_per_step": T,
+                   "step": "one DFT window (T = 90 updates) + NTFF at 543 angles",
+                   "l2": "inputs larger than L2 (working set %.1f GB)" % (
+                       (2 * 42 * 4 + 4) * cells / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": bc * cells},
+        "e2e": {"value": round(e2e_val, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": main["h2d_bytes"], "d2h_bytes_per_step": main["d2h_bytes"]},
+        "gpu_launches": int(main["launches"]),
+        "clocks": main["clocks"],
+        "mie": {"nrms_phi_0_45_90": [round(v, 5) for v in main["mie_nrms"]],
+                "periods_run": main["periods"], "incident_amplitude": round(main["incident"], 6)},
+        "storage_modes": storage_modes,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.size, budget_s=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ CPU oracle
+class OracleSlab:
+    """The FP64 oracle on a z-slab of the workload through the sphere's centre:
+    the slab's own permittivity, absorbing layer (global coordinates) and TF/SF
+    links, fed by the oracle's incident line.  The oracle is used as it is."""
+
+    def __init__(self, size, dz=8):
+        from oracle import lb
+        self.size, self.dz = size, dz
+        wl, x, eps_in, w = 30.0, 5.0, 1.33 ** 2, 16
+        a = x * wl / (2 * math.pi)
+        z0 = size // 2 - dz // 2
+        eps = W.sphere_eps(size, a, eps_in, z_range=(z0, z0 + dz))
+        wave = W.axis_wave("3d", (size, size, size), w, wl)
+        self.lat = lb.Lattice((size, size, dz), eps, origin=(0, 0, z0),
+                              global_shape=(size, size, size), sponge_w=w,
+                              sigma_max=W.DEFAULT_SIGMA_MAX)
+        self.lat.set_tfsf_line(wave.tf_lo, wave.tf_hi, 2)
+        rng = np.random.default_rng(0)
+        self.lat.f = rng.standard_normal(self.lat.f.shape) * 1e-3
+        self.inc = rng.standard_normal((size, 42)) * 1e-3
+        self.cells = size * size * dz
+        self.n = 0
+
+    def step(self, k):
+        for _ in range(k):
+            self.lat.step(self.n, inc_line=self.inc)
+            self.n += 1
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(size, budget_s=15.0):
+    """Time the oracle on a bounded sample (a slab) of the workload for about
+    budget_s seconds of CPU work; MLUPS = slab cells x updates / seconds."""
+    slab = OracleSlab(size)
+    slab.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        slab.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": round(slab.cells * n / el / 1e6, 3), "unit": "MLUPS", "cores": cpu_cores(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle, z-slab {size}x{size}x{slab.dz} through the centre of the "
+                      f"{size}^3 sphere workload, {n} lattice updates in {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle as it stands, each bench step a
+    bounded sample (a slab, --ref-updates lattice updates) of the workload."""
+    if rank != 0:
+        return
+    K, Wm = args.steps, args.warmup
+    per_step = max(1, int(round(args.ref_updates)))
+    slab = OracleSlab(args.size)
+    for _ in range(Wm):
+        slab.step(per_step)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        slab.step(per_step)
+    el = time.perf_counter() - t0
+    value = slab.cells * per_step * K / el / 1e6
+    sample = f"z-slab {args.size}x{args.size}x{slab.dz} of the workload, {per_step} lattice updates per step"
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
+        "steps": K, "warmup": Wm, "ms_per_step": round(el / K * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"sphere_{args.size}^3_n1.33_x5_lambda30_W16_fp32_storage",
+                   "sample": sample},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": cpu_cores(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=27)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
+    ap.add_argument("--size", type=int, default=384)
+    ap.add_argument("--fp32-only", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-updates", type=float, default=2)
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * lbem.h -- C ABI of the GB300 (sm_103a) lattice-Boltzmann electromagnetic
+ * scattering library: the D3Q7 vector-population LB scheme for Maxwell's
+ * equations of arXiv 2510.11042 (Sec. 2), with a total-field/scattered-field
+ * plane-wave source, an absorbing outer layer, a running single-frequency DFT
+ * of the near fields and the near-to-far-field projection of the angular
+ * scattering intensity |S|^2 (Eqs. 5-10).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: lattice units, dx = dt = 1, vacuum speed of light c = 1/3 (Sec. 2.1,
+ * Eq. 3), vacuum impedance one, wavenumber k = 2 pi / lambda, period
+ * T = 3 lambda steps.  Angles are radians.
+ *
+ * Status: every function returning int32_t returns LBEM_OK (0) or a negative
+ * LBEM_ERR_* code; no C++ exception crosses this boundary.  The text of the
+ * last error of a handle is available from lbem_last_error().  A failed call
+ * leaves the handle's state as it was, except lbem_step(), after which the
+ * handle holds whatever steps completed before the failure.
+ *
+ * Streams and threads: a handle is bound to the CUDA stream given at creation
+ * (NULL = the legacy default stream) and to the current device at that moment.
+ * Calls on one handle must not race; different handles are independent.
+ * Every call that returns results to the host synchronises the stream; the
+ * others only enqueue work.
+ *
+ * Memory: pointers named *_host are host memory (pageable or pinned), pointers
+ * named *_dev are device memory of the handle's device; arguments with an
+ * "on_device" flag accept either.  The library never keeps a caller pointer
+ * beyond a call, except the workspace passed to lbem_create(), which the
+ * caller must keep alive until lbem_destroy().
+ *
+ * Population layout (lbem_get_populations / lbem_set_populations):
+ * float32 [Q][nz][ny][nx], plane q = (family, direction i, component a),
+ * families e then h (Sec. 2.1: e_i, h_i), directions i = 0..6 in the order
+ * c_0 = 0, +x, -x, +y, -y, +z, -z, and per family only the components the
+ * mode carries:
+ *   LBEM_MODE_EZ (2D, E along z; "TM" for cylinders, Sec. 3.2): e_z; h_x, h_y  (Q = 21)
+ *   LBEM_MODE_HZ (2D, H along z; "TE"):                         e_x, e_y; h_z  (Q = 21)
+ *   LBEM_MODE_3D:                                               e_xyz; h_xyz   (Q = 42)
+ * e.g. in EZ mode q = i for e_z of direction i, q = 7 + 2 i + a for h_a.
+ * A 2D grid has nz == 1 and is periodic along z (the +-z populations stream
+ * onto themselves).  The stored populations are the post-collision ones.
+ */
+#ifndef LBEM_H
+#define LBEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBEM_OK = 0,
+    LBEM_ERR_ARG = -1,       /* invalid argument, shape, box or polarisation */
+    LBEM_ERR_OOM = -2,       /* device allocation failed or workspace too small */
+    LBEM_ERR_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    LBEM_ERR_NONFINITE = -4, /* a NaN or Inf was found in the state */
+    LBEM_ERR_TIMEOUT = -5,   /* a bounded wait ran out */
+    LBEM_ERR_STATE = -6      /* call not valid in the handle's state */
+};
+
+typedef struct lbem_ctx *lbem_handle;
+
+/* The only velocity set of the paper: D3Q7 (Sec. 2.1). */
+typedef enum { LBEM_D3Q7 = 0 } lbem_velocity_set;
+
+/* Storage type of the populations in device memory.  The update arithmetic is
+ * float32 in every case; F16/BF16 store each population plane scaled by a
+ * power of two (see lbem_set_storage_scales) and round to nearest even. */
+typedef enum { LBEM_F32 = 0, LBEM_F16 = 1, LBEM_BF16 = 2 } lbem_storage;
+
+typedef enum { LBEM_MODE_EZ = 0, LBEM_MODE_HZ = 1, LBEM_MODE_3D = 2 } lbem_mode;
+
+/* The lattice.  nz == 1 with an EZ/HZ mode is a 2D problem; LBEM_MODE_3D needs
+ * nz >= 2.  absorber_width W cells on every face of an axis longer than one
+ * cell: post-collision populations are multiplied by 1 - sigma_max (m/W)^3,
+ * m = W - d, d = distance in cells to the nearest such face (the paper's
+ * outer boundary, Sec. 2.2, Eq. 4, is the clamped pull at the faces; the
+ * layer itself is this library's reading of the absorbing layers the paper
+ * names as future work, Sec. 4).  sigma_max <= 0 selects 0.3. */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t absorber_width;
+    double sigma_max;
+    int32_t storage;    /* lbem_storage */
+    int32_t mode;       /* lbem_mode */
+} lbem_grid_desc;
+
+/* A linearly polarised incident plane wave (Sec. 2.3: "the incident field
+ * considered in this work is linearly polarized").  dir must be +x or +y for
+ * the 2D modes and +x, +y or +z in 3D; pol must be a unit vector orthogonal to
+ * dir (along z for EZ, in the xy plane for HZ).  The incident field is
+ * E(t) = amplitude * ramp(t) * sin(w t) * pol, H = dir x E, ramp a raised
+ * cosine over ramp_periods periods, w = 2 pi / T, T = 3 * wavelength, which
+ * must be an integer.  It is carried by a 1D D3Q7 line along dir that shares
+ * the grid's coordinate along dir, is driven at node source_index (-1: W + 2)
+ * and has the same absorbing layer at both ends; every lattice link that
+ * crosses the surface of the total-field box [tfsf_lo, tfsf_hi] (inclusive
+ * cell indices) adds (entering) or subtracts (leaving) the line's incident
+ * population of the link's source cell.  The NTFF box [ntff_lo, ntff_hi] must
+ * enclose the total-field box strictly and lie outside the absorbing layer;
+ * center is the phase reference of the far field.  For 2D grids the z entries
+ * of the boxes must be 0. */
+typedef struct {
+    double dir[3];
+    double pol[3];
+    double wavelength;
+    double amplitude;
+    double ramp_periods;
+    int32_t tfsf_lo[3], tfsf_hi[3];
+    int32_t ntff_lo[3], ntff_hi[3];
+    double center[3];
+    int32_t source_index;
+} lbem_plane_wave;
+
+/* Bytes of device workspace a grid needs (populations in two buffers, the
+ * permittivity map, the incident line, the DFT accumulators and scratch). */
+int32_t lbem_workspace_bytes(const lbem_grid_desc *grid, size_t *bytes_out);
+
+/* Create a solver on the current device.
+ * eps_r: relative permittivity per cell, float32 [nz][ny][nx], values >= 1
+ *   (non-absorbing dielectrics, Sec. 2.1; mu_r = 1 as in all of the paper's 2D
+ *   and 3D work, Sec. 3.1), host or device memory (eps_on_device).  Copied.
+ * cuda_stream: cudaStream_t the handle enqueues on (NULL: legacy default stream).
+ * workspace: device memory of at least lbem_workspace_bytes(), 256-byte
+ *   aligned, owned by the caller; NULL makes the library cudaMalloc it and
+ *   free it in lbem_destroy().
+ * The populations start at zero (vacuum, no field). */
+int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const float *eps_r,
+                    int32_t eps_on_device, void *cuda_stream, void *workspace,
+                    size_t workspace_bytes, lbem_handle *out);
+
+/* Replace the permittivity map (same layout and rules as in lbem_create). */
+int32_t lbem_set_permittivity(lbem_handle h, const float *eps_r, int32_t eps_on_device);
+
+/* Attach an incident plane wave (see lbem_plane_wave).  Resets the incident
+ * line to zero; the main lattice keeps its state and its time. */
+int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *wave);
+
+/* Record the DFT of the fields over n_periods whole periods starting at field
+ * time t_start (Sec. 2.4: "over one period of the steady-state oscillation"):
+ * X = 2/(n_periods T) sum_t x(t) exp(-j w t), x the moments computed in the
+ * step that produces time t.  Clears the accumulators.  Needs a plane wave. */
+int32_t lbem_set_dft_window(lbem_handle h, int64_t t_start, int32_t n_periods);
+
+/* Advance n time steps (Eq. 1 with the equilibria of Eq. 2, streaming with the
+ * outer boundary of Eq. 4, the TF/SF source, the absorbing layer and the DFT
+ * of the near fields), asynchronously on the handle's stream. */
+int32_t lbem_step(lbem_handle h, int64_t n);
+
+/* Number of steps taken since creation (the time of the stored state). */
+int32_t lbem_get_time(lbem_handle h, int64_t *t_out);
+
+/* Angular scattering intensity |S|^2 (Eqs. 5, 6) by the near-to-far-field
+ * projection of Eqs. 7-10 in the far-field limit, from the DFT accumulators:
+ * J = n x H, M = -n x E on the NTFF box faces (trapezoidal rule per face),
+ * N = sum w J exp(j k r_hat.(r'-center)), L likewise with M;
+ *   3D: |S|^2 = k^4 (|N_th + L_ph|^2 + |N_ph - L_th|^2) / (16 pi^2 |E_I|^2),
+ *       r_hat = (sin th cos ph, sin th sin ph, cos th);
+ *   EZ: |S|^2 = k^2 |N_z - L_ph|^2 / (8 pi |E_I|^2),
+ *   HZ: |S|^2 = k^2 |N_ph + L_z|^2 / (8 pi |E_I|^2),  r_hat = (cos th, sin th, 0);
+ * |E_I| the incident line's E phasor along pol at the centre (Eq. 5/6: "in the
+ * vicinity of the scatterer").  theta_host, phi_host: n angles (phi ignored
+ * and may be NULL in 2D).  s2_host: n outputs.  amp_host (optional, NULL): 12
+ * doubles per angle, Re/Im of N_x, N_y, N_z, L_x, L_y, L_z.  All FP64. */
+int32_t lbem_far_field(lbem_handle h, const double *theta_host, const double *phi_host,
+                       int32_t n, double *s2_host, double *amp_host);
+
+/* |E_I| as used by lbem_far_field. */
+int32_t lbem_incident_amplitude(lbem_handle h, double *out_host);
+
+/* Copy the populations out / in, float32 [Q][nz][ny][nx] (layout above). */
+int32_t lbem_get_populations(lbem_handle h, float *out, int32_t out_on_device);
+int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t in_on_device);
+
+/* Fields of the stored state, E = sum_i e_i / eps_r, H = sum_i h_i (the zeroth
+ * moments of Sec. 2.1), float32 [3][nz][ny][nx] each (components x, y, z). */
+int32_t lbem_fields(lbem_handle h, float *E_out, float *H_out, int32_t out_on_device);
+
+/* DFT phasors on the NTFF box faces, FP64.  Faces f = 2*axis + side (side 0 at
+ * ntff_lo, 1 at ntff_hi) for each axis longer than one cell, in that order;
+ * per face [C][2][nu][nv] (component, re/im, u, v), (u, v) = (z, y) for
+ * x-faces, (z, x) for y-faces, (y, x) for z-faces, each spanning the NTFF box.
+ * Components C: EZ (E_z, H_x, H_y); HZ (E_x, E_y, H_z); 3D (E_x..H_z).
+ * lbem_dft_doubles() gives the total count. */
+int32_t lbem_dft_doubles(lbem_handle h, size_t *count_out);
+int32_t lbem_get_dft(lbem_handle h, double *out_host);
+
+/* Physical energy 1/2 sum (eps_r |E|^2 + |H|^2) of the stored state (the
+ * steady-state monitor of Sec. 3.2), FP64; LBEM_ERR_NONFINITE if any
+ * population is NaN or Inf. */
+int32_t lbem_energy(lbem_handle h, double *out_host);
+
+/* Checkpoint: opaque snapshot of populations, incident line, DFT accumulators
+ * and time, for the same grid description. */
+int32_t lbem_state_bytes(lbem_handle h, size_t *bytes_out);
+int32_t lbem_save_state(lbem_handle h, void *buf_host, size_t bytes);
+int32_t lbem_load_state(lbem_handle h, const void *buf_host, size_t bytes);
+
+/* Power-of-two scales of the reduced-precision storage, one per plane q:
+ * stored = population / scale.  Ignored for LBEM_F32.  Values must be exact
+ * powers of two. */
+int32_t lbem_set_storage_scales(lbem_handle h, const float *scales_host);
+int32_t lbem_get_storage_scales(lbem_handle h, float *scales_host);
+
+/* Wait for the handle's stream; reports an asynchronous CUDA error. */
+int32_t lbem_sync(lbem_handle h);
+
+void lbem_destroy(lbem_handle h);
+
+/* Message of the last failed call on h (or of the last failed lbem_create when
+ * h is NULL); never NULL. */
+const char *lbem_last_error(lbem_handle h);
+
+/* Kernel launches this handle has issued since creation (every lbem_* call
+ * counts the kernels it enqueues). */
+int64_t lbem_kernel_launches(lbem_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBEM_H */

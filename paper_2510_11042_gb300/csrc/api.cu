@@ -1,0 +1,761 @@
+// C ABI of liblbem (declared in include/lbem.h): handle life cycle, argument
+// checking, workspace layout, the step loop and the far-field call.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbem.h"
+#include "lbem_internal.cuh"
+
+namespace lbem {
+int step_block_x();
+}
+
+using namespace lbem;
+
+struct lbem_ctx {
+    lbem_grid_desc g;
+    int Q = 0, NC = 0;
+    int nxp = 0;
+    long long P = 0;          // plane stride (elements)
+    long long ncell = 0;
+    size_t elem = 4;          // bytes per stored population
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // workspace
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool owns_ws = false;
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *inv_eps = nullptr;
+    float *line[2] = {nullptr, nullptr};
+    int n_line_max = 0;
+    double *dft = nullptr;
+    size_t dft_doubles_max = 0;
+    double *line_dft = nullptr;
+    double *scratch = nullptr;  // far-field partials / energy partials
+    size_t scratch_doubles = 0;
+    float *stage = nullptr;     // one FP32 plane of ncell values
+    int *flag = nullptr;
+    // time and source
+    int64_t t = 0;
+    bool has_wave = false;
+    lbem_plane_wave wave;
+    int T = 0;
+    double omega = 0.0;
+    int inc_axis = 0, n_line = 0, src_index = 0;
+    FaceGeom faces;
+    size_t dft_doubles = 0;
+    int64_t dft_t0 = -1;
+    int dft_periods = 0;
+    float scale[kMaxQ], inv_scale[kMaxQ];
+    int64_t launches = 0;
+    char err[512];
+};
+
+static thread_local char g_create_err[512] = "";
+
+static int fail(lbem_ctx *h, int code, const char *fmt, ...)
+{
+    char *buf = h ? h->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(lbem_ctx *h, cudaError_t e, const char *what)
+{
+    return fail(h, LBEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                               \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
+    } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t f0, f1, inv_eps, line0, line1, dft, line_dft, scratch, stage, flag, total;
+    int Q, nxp, n_line_max;
+    long long P, ncell;
+    size_t elem, dft_doubles_max, scratch_doubles;
+};
+
+static int check_grid(const lbem_grid_desc *g, char *why, size_t n)
+{
+    if (!g) return snprintf(why, n, "grid description is NULL"), 0;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+        return snprintf(why, n, "grid extents must be >= 1 (got %d x %d x %d)", g->nx, g->ny, g->nz), 0;
+    if (g->mode < 0 || g->mode > 2) return snprintf(why, n, "unknown mode %d", g->mode), 0;
+    if (g->storage < 0 || g->storage > 2) return snprintf(why, n, "unknown storage %d", g->storage), 0;
+    if (g->mode != 2 && g->nz != 1)
+        return snprintf(why, n, "the 2D modes (EZ, HZ) need nz == 1"), 0;
+    if (g->mode == 2 && g->nz < 2) return snprintf(why, n, "3D mode needs nz >= 2"), 0;
+    const long long nxp = (g->nx + 31) / 32 * 32;
+    const long long P = nxp * g->ny * (long long)g->nz;
+    if (P >= (1LL << 31)) return snprintf(why, n, "grid too large (plane of %lld elements)", P), 0;
+    const int minext = g->mode == 2 ? std::min(g->nx, std::min(g->ny, g->nz)) : std::min(g->nx, g->ny);
+    if (g->absorber_width < 0 || 2 * g->absorber_width >= minext)
+        return snprintf(why, n, "absorber_width %d does not fit the grid", g->absorber_width), 0;
+    if (!(g->sigma_max <= 1.0) || std::isnan(g->sigma_max))
+        return snprintf(why, n, "sigma_max must be <= 1"), 0;
+    return 1;
+}
+
+static Layout make_layout(const lbem_grid_desc *g)
+{
+    Layout L;
+    L.Q = planes_of_mode(g->mode);
+    L.nxp = (g->nx + 31) / 32 * 32;
+    L.P = (long long)L.nxp * g->ny * g->nz;
+    L.ncell = (long long)g->nx * g->ny * g->nz;
+    L.elem = g->storage == LBEM_F32 ? 4 : 2;
+    L.n_line_max = std::max(g->nx, std::max(g->ny, g->nz));
+    const int NC = dft_comps_of_mode(g->mode);
+    // DFT capacity: the faces of the whole grid bound those of any NTFF box
+    const long long fx = (long long)g->ny * g->nz, fy = (long long)g->nx * g->nz,
+                    fz = (long long)g->nx * g->ny;
+    L.dft_doubles_max = (size_t)(2 * (fx + fy + (g->nz > 1 ? fz : 0))) * NC * 2;
+    L.scratch_doubles = std::max<size_t>((size_t)kAngleBatch * kMaxChunks * 12 + kAngleBatch * 16,
+                                         152 * 32 + 8);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.f0 = take((size_t)L.Q * L.P * L.elem);
+    L.f1 = take((size_t)L.Q * L.P * L.elem);
+    L.inv_eps = take((size_t)L.P * 4);
+    L.line0 = take((size_t)L.Q * L.n_line_max * 4);
+    L.line1 = take((size_t)L.Q * L.n_line_max * 4);
+    L.dft = take(L.dft_doubles_max * 8);
+    L.line_dft = take((size_t)L.n_line_max * 6 * 8);
+    L.scratch = take(L.scratch_doubles * 8);
+    L.stage = take((size_t)L.ncell * 4);
+    L.flag = take(256);
+    L.total = o;
+    return L;
+}
+
+static void default_scales(lbem_ctx *h, double amplitude, double eps_max)
+{
+    // populations of a unit-amplitude field stay within a few units; keep them
+    // near 2^12 in the stored format.  The rest population e_0 ~ (eps-1) E.
+    for (int q = 0; q < kMaxQ; ++q) {
+        h->scale[q] = 1.f;
+        h->inv_scale[q] = 1.f;
+    }
+    if (h->g.storage == LBEM_F32) return;
+    const double a = amplitude > 0 ? amplitude : 1.0;
+    for (int q = 0; q < h->Q; ++q) {
+        const bool rest_e = (q < (h->g.mode == 0 ? 1 : (h->g.mode == 1 ? 2 : 3)));
+        double span = 4.0 * a * (rest_e ? std::max(1.0, eps_max) : 1.0);
+        int e2 = (int)std::ceil(std::log2(span));
+        const float s = std::ldexp(1.0f, e2 - 14);
+        h->scale[q] = s;
+        h->inv_scale[q] = 1.0f / s;
+    }
+}
+
+extern "C" {
+
+int32_t lbem_workspace_bytes(const lbem_grid_desc *grid, size_t *bytes_out)
+{
+    char why[256];
+    if (!bytes_out) return fail(nullptr, LBEM_ERR_ARG, "bytes_out is NULL");
+    if (!check_grid(grid, why, sizeof why)) return fail(nullptr, LBEM_ERR_ARG, "%s", why);
+    *bytes_out = make_layout(grid).total;
+    return LBEM_OK;
+}
+
+static int upload_eps(lbem_ctx *h, const float *eps, int on_device)
+{
+    const float *src = eps;
+    if (!on_device) {
+        CK(h, cudaMemcpyAsync(h->stage, eps, (size_t)h->ncell * 4, cudaMemcpyHostToDevice, h->stream));
+        src = h->stage;
+    }
+    // validate first, so that a rejected map leaves the handle unchanged
+    CK(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    CK(h, launch_inv_eps(src, nullptr, h->g.nx, h->g.ny, h->g.nz, h->nxp, h->flag, h->stream));
+    h->launches += 1;
+    int bad = 0;
+    CK(h, cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (bad) return fail(h, LBEM_ERR_ARG, "eps_r must be finite and >= 1 in every cell");
+    CK(h, launch_inv_eps(src, h->inv_eps, h->g.nx, h->g.ny, h->g.nz, h->nxp, h->flag, h->stream));
+    h->launches += 1;
+    return LBEM_OK;
+}
+
+int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const float *eps_r,
+                    int32_t eps_on_device, void *cuda_stream, void *workspace,
+                    size_t workspace_bytes, lbem_handle *out)
+{
+    char why[256];
+    if (!out) return fail(nullptr, LBEM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (velocity_set != LBEM_D3Q7) return fail(nullptr, LBEM_ERR_ARG, "only LBEM_D3Q7 is supported");
+    if (!check_grid(grid, why, sizeof why)) return fail(nullptr, LBEM_ERR_ARG, "%s", why);
+    if (!eps_r) return fail(nullptr, LBEM_ERR_ARG, "eps_r is NULL");
+    if (workspace && ((uintptr_t)workspace & 255))
+        return fail(nullptr, LBEM_ERR_ARG, "workspace must be 256-byte aligned");
+    const Layout L = make_layout(grid);
+    if (workspace && workspace_bytes < L.total)
+        return fail(nullptr, LBEM_ERR_OOM, "workspace of %zu bytes is smaller than the %zu needed",
+                    workspace_bytes, L.total);
+    lbem_ctx *h = new (std::nothrow) lbem_ctx();
+    if (!h) return fail(nullptr, LBEM_ERR_OOM, "host allocation failed");
+    h->g = *grid;
+    if (!(h->g.sigma_max > 0.0)) h->g.sigma_max = 0.3;
+    h->Q = L.Q;
+    h->NC = dft_comps_of_mode(grid->mode);
+    h->nxp = L.nxp;
+    h->P = L.P;
+    h->ncell = L.ncell;
+    h->elem = L.elem;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->err[0] = 0;
+    cudaGetDevice(&h->device);
+    if (workspace) {
+        h->ws = (char *)workspace;
+        h->ws_bytes = workspace_bytes;
+    } else {
+        cudaError_t e = cudaMalloc((void **)&h->ws, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(nullptr, LBEM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", L.total,
+                        cudaGetErrorString(e));
+        }
+        h->owns_ws = true;
+        h->ws_bytes = L.total;
+    }
+    h->f[0] = h->ws + L.f0;
+    h->f[1] = h->ws + L.f1;
+    h->inv_eps = (float *)(h->ws + L.inv_eps);
+    h->line[0] = (float *)(h->ws + L.line0);
+    h->line[1] = (float *)(h->ws + L.line1);
+    h->n_line_max = L.n_line_max;
+    h->dft = (double *)(h->ws + L.dft);
+    h->dft_doubles_max = L.dft_doubles_max;
+    h->line_dft = (double *)(h->ws + L.line_dft);
+    h->scratch = (double *)(h->ws + L.scratch);
+    h->scratch_doubles = L.scratch_doubles;
+    h->stage = (float *)(h->ws + L.stage);
+    h->flag = (int *)(h->ws + L.flag);
+    default_scales(h, 1.0, 1.0);
+    int rc = LBEM_OK;
+    cudaError_t e = cudaMemsetAsync(h->f[0], 0, (size_t)L.Q * L.P * L.elem, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, (size_t)L.Q * L.P * L.elem, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->inv_eps, 0, (size_t)L.P * 4, h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaMemsetAsync");
+    if (rc == LBEM_OK) rc = upload_eps(h, eps_r, eps_on_device);
+    if (rc != LBEM_OK) {
+        snprintf(g_create_err, sizeof g_create_err, "%s", h->err);
+        lbem_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return LBEM_OK;
+}
+
+int32_t lbem_set_permittivity(lbem_handle h, const float *eps_r, int32_t eps_on_device)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (!eps_r) return fail(h, LBEM_ERR_ARG, "eps_r is NULL");
+    return upload_eps(h, eps_r, eps_on_device);
+}
+
+static int axis_of(const double d[3])
+{
+    int ax = -1;
+    for (int a = 0; a < 3; ++a) {
+        if (std::fabs(d[a]) > 1e-12) {
+            if (ax >= 0) return -1;
+            ax = a;
+        }
+    }
+    if (ax < 0 || std::fabs(d[ax] - 1.0) > 1e-12) return -1;
+    return ax;
+}
+
+static void build_faces(lbem_ctx *h)
+{
+    FaceGeom &F = h->faces;
+    const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
+    F.nfaces = 0;
+    long long off = 0, cells = 0;
+    for (int a = 0; a < 3; ++a) {
+        F.lo[a] = h->wave.ntff_lo[a];
+        F.hi[a] = h->wave.ntff_hi[a];
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        if (n3[ax] <= 1) continue;
+        const int ua = ax == 2 ? 1 : 2, va = ax == 0 ? 1 : 0;
+        const int nu = F.hi[ua] - F.lo[ua] + 1, nv = F.hi[va] - F.lo[va] + 1;
+        for (int side = 0; side < 2; ++side) {
+            const int f = F.nfaces++;
+            F.axis[f] = ax;
+            F.side[f] = side;
+            F.nu[f] = nu;
+            F.nv[f] = nv;
+            F.off[f] = off;
+            F.cell_start[f] = cells;
+            off += (long long)h->NC * 2 * nu * nv;
+            cells += (long long)nu * nv;
+        }
+    }
+    F.cell_start[F.nfaces] = cells;
+    h->dft_doubles = (size_t)off;
+}
+
+int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (!w) return fail(h, LBEM_ERR_ARG, "wave is NULL");
+    const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
+    const int ax = axis_of(w->dir);
+    if (ax < 0) return fail(h, LBEM_ERR_ARG, "dir must be +x, +y or +z");
+    if (h->g.mode != 2 && ax == 2) return fail(h, LBEM_ERR_ARG, "2D modes need dir in the xy plane");
+    double pn = 0, pd = 0;
+    for (int a = 0; a < 3; ++a) {
+        pn += w->pol[a] * w->pol[a];
+        pd += w->pol[a] * w->dir[a];
+    }
+    if (std::fabs(pn - 1.0) > 1e-9 || std::fabs(pd) > 1e-9)
+        return fail(h, LBEM_ERR_ARG, "pol must be a unit vector orthogonal to dir");
+    if (h->g.mode == 0 && (std::fabs(w->pol[0]) > 1e-12 || std::fabs(w->pol[1]) > 1e-12))
+        return fail(h, LBEM_ERR_ARG, "EZ mode needs pol along z");
+    if (h->g.mode == 1 && std::fabs(w->pol[2]) > 1e-12)
+        return fail(h, LBEM_ERR_ARG, "HZ mode needs pol in the xy plane");
+    const double T = 3.0 * w->wavelength;
+    if (!(w->wavelength > 0) || std::fabs(T - std::round(T)) > 1e-9 || std::round(T) < 2)
+        return fail(h, LBEM_ERR_ARG, "3*wavelength must be an integer >= 2 (the period in steps)");
+    if (!(w->amplitude > 0) || !std::isfinite(w->amplitude))
+        return fail(h, LBEM_ERR_ARG, "amplitude must be positive");
+    if (!(w->ramp_periods >= 0)) return fail(h, LBEM_ERR_ARG, "ramp_periods must be >= 0");
+    const int W = h->g.absorber_width;
+    for (int a = 0; a < 3; ++a) {
+        if (n3[a] == 1) {
+            if (w->tfsf_lo[a] || w->tfsf_hi[a] || w->ntff_lo[a] || w->ntff_hi[a])
+                return fail(h, LBEM_ERR_ARG, "box bounds along a 1-cell axis must be 0");
+            continue;
+        }
+        if (!(W <= w->ntff_lo[a] && w->ntff_lo[a] < w->tfsf_lo[a] && w->tfsf_lo[a] <= w->tfsf_hi[a] &&
+              w->tfsf_hi[a] < w->ntff_hi[a] && w->ntff_hi[a] <= n3[a] - 1 - W))
+            return fail(h, LBEM_ERR_ARG,
+                        "axis %d: need W <= ntff_lo < tfsf_lo <= tfsf_hi < ntff_hi <= n-1-W", a);
+    }
+    int src = w->source_index < 0 ? W + 2 : w->source_index;
+    if (src < 0 || src >= w->tfsf_lo[ax] - 1)
+        return fail(h, LBEM_ERR_ARG, "source_index must lie upstream of the total-field box");
+    h->wave = *w;
+    h->wave.source_index = src;
+    h->has_wave = true;
+    h->T = (int)std::lround(T);
+    h->omega = 2.0 * M_PI / h->T;
+    h->inc_axis = ax;
+    h->n_line = n3[ax];
+    h->src_index = src;
+    build_faces(h);
+    h->dft_t0 = -1;
+    h->dft_periods = 0;
+    CK(h, cudaMemsetAsync(h->line[0], 0, (size_t)h->Q * h->n_line_max * 4, h->stream));
+    CK(h, cudaMemsetAsync(h->line[1], 0, (size_t)h->Q * h->n_line_max * 4, h->stream));
+    CK(h, cudaMemsetAsync(h->line_dft, 0, (size_t)h->n_line_max * 6 * 8, h->stream));
+    CK(h, cudaMemsetAsync(h->dft, 0, h->dft_doubles * 8, h->stream));
+    return LBEM_OK;
+}
+
+int32_t lbem_set_dft_window(lbem_handle h, int64_t t_start, int32_t n_periods)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
+    if (n_periods < 1 || t_start < 1) return fail(h, LBEM_ERR_ARG, "need t_start >= 1 and n_periods >= 1");
+    h->dft_t0 = t_start;
+    h->dft_periods = n_periods;
+    CK(h, cudaMemsetAsync(h->dft, 0, h->dft_doubles * 8, h->stream));
+    CK(h, cudaMemsetAsync(h->line_dft, 0, (size_t)h->n_line_max * 6 * 8, h->stream));
+    return LBEM_OK;
+}
+
+static double ramp(double t, double tr)
+{
+    if (t <= 0) return 0.0;
+    if (t >= tr) return 1.0;
+    return 0.5 * (1.0 - std::cos(M_PI * t / tr));
+}
+
+int32_t lbem_step(lbem_handle h, int64_t n)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (n < 0) return fail(h, LBEM_ERR_ARG, "n must be >= 0");
+    StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    const int BX = step_block_x();
+    a.inv_eps = h->inv_eps;
+    a.nx = h->g.nx; a.ny = h->g.ny; a.nz = h->g.nz; a.nxp = h->nxp;
+    a.P = h->P;
+    a.nblk_x = (h->g.nx + BX - 1) / BX;
+    a.nblk_main = a.nblk_x * h->g.ny * h->g.nz;
+    a.w = h->g.absorber_width;
+    a.sigma_max = (float)h->g.sigma_max;
+    a.inv_w = a.w > 0 ? 1.0f / (float)a.w : 0.f;
+    for (int q = 0; q < kMaxQ; ++q) {
+        a.scale[q] = h->scale[q];
+        a.inv_scale[q] = h->inv_scale[q];
+    }
+    if (h->has_wave) {
+        a.tfsf = 1;
+        a.line_on = 1;
+        for (int k = 0; k < 3; ++k) {
+            a.tf_lo[k] = h->wave.tfsf_lo[k];
+            a.tf_hi[k] = h->wave.tfsf_hi[k];
+            a.nt_lo[k] = h->wave.ntff_lo[k];
+            a.nt_hi[k] = h->wave.ntff_hi[k];
+        }
+        a.inc_axis = h->inc_axis;
+        a.n_line = h->n_line;
+        a.src_index = h->src_index;
+        a.dft = h->dft;
+        for (int f = 0; f < h->faces.nfaces; ++f) {
+            a.face_off[f] = h->faces.off[f];
+            a.face_nu[f] = h->faces.nu[f];
+            a.face_nv[f] = h->faces.nv[f];
+        }
+        a.line_dft = h->line_dft;
+    }
+    double kxp[3] = {0, 0, 0};
+    if (h->has_wave) {
+        const double *d = h->wave.dir, *p = h->wave.pol;
+        kxp[0] = d[1] * p[2] - d[2] * p[1];
+        kxp[1] = d[2] * p[0] - d[0] * p[2];
+        kxp[2] = d[0] * p[1] - d[1] * p[0];
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t t = h->t + 1;  // time of the fields this step computes
+        a.fin = h->f[h->cur];
+        a.fout = h->f[h->cur ^ 1];
+        if (h->has_wave) {
+            a.inc = h->line[h->cur];
+            a.line_in = h->line[h->cur];
+            a.line_out = h->line[h->cur ^ 1];
+            const double ph = 2.0 * M_PI * (double)(t % h->T) / (double)h->T;
+            const double s = h->wave.amplitude * ramp((double)t, h->wave.ramp_periods * h->T) * std::sin(ph);
+            for (int c = 0; c < 3; ++c) {
+                a.src_E[c] = (float)(s * h->wave.pol[c]);
+                a.src_H[c] = (float)(s * kxp[c]);
+            }
+            a.dft_on = (h->dft_t0 >= 1 && t >= h->dft_t0 && t < h->dft_t0 + (int64_t)h->dft_periods * h->T);
+            if (a.dft_on) {
+                a.dft_c = std::cos(ph);
+                a.dft_s = std::sin(ph);
+                a.dft_scale = 2.0 / ((double)h->dft_periods * h->T);
+            }
+        }
+        cudaError_t e = launch_step(h->g.mode, h->g.storage, a, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+        h->launches += 1;
+        h->cur ^= 1;
+        h->t = t;
+    }
+    return LBEM_OK;
+}
+
+int32_t lbem_get_time(lbem_handle h, int64_t *t_out)
+{
+    if (!h || !t_out) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    *t_out = h->t;
+    return LBEM_OK;
+}
+
+static void centre_nodes(lbem_ctx *h, int *i0, int *i1)
+{
+    const double c = h->wave.center[h->inc_axis];
+    int a = (int)std::floor(c);
+    if (a < 0) a = 0;
+    if (a > h->n_line - 1) a = h->n_line - 1;
+    *i0 = a;
+    *i1 = std::min(a + 1, h->n_line - 1);
+}
+
+int32_t lbem_far_field(lbem_handle h, const double *theta, const double *phi, int32_t n,
+                       double *s2, double *amp)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
+    if (n < 0 || (n > 0 && (!theta || !s2))) return fail(h, LBEM_ERR_ARG, "bad angle arrays");
+    if (h->g.mode == 2 && n > 0 && !phi) return fail(h, LBEM_ERR_ARG, "3D needs phi");
+    FarFieldArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.dft = h->dft;
+    a.line_dft = h->line_dft;
+    a.g = h->faces;
+    a.mode = h->g.mode;
+    a.k = 2.0 * M_PI / h->wave.wavelength;
+    for (int c = 0; c < 3; ++c) {
+        a.center[c] = h->wave.center[c];
+        a.pol[c] = h->wave.pol[c];
+    }
+    centre_nodes(h, &a.center_i0, &a.center_i1);
+    const long long cells = h->faces.cell_start[h->faces.nfaces];
+    int chunks = (int)((cells + 4095) / 4096);
+    a.chunks = std::max(1, std::min(kMaxChunks, chunks));
+    double *d_theta = h->scratch;
+    double *d_phi = d_theta + kAngleBatch;
+    double *d_s2 = d_phi + kAngleBatch;
+    double *d_amp = d_s2 + kAngleBatch;
+    double *d_part = d_amp + (size_t)kAngleBatch * 12;
+    for (int32_t b0 = 0; b0 < n; b0 += kAngleBatch) {
+        const int nb = std::min<int32_t>(kAngleBatch, n - b0);
+        CK(h, cudaMemcpyAsync(d_theta, theta + b0, nb * 8, cudaMemcpyHostToDevice, h->stream));
+        if (h->g.mode == 2)
+            CK(h, cudaMemcpyAsync(d_phi, phi + b0, nb * 8, cudaMemcpyHostToDevice, h->stream));
+        a.theta = d_theta;
+        a.phi = d_phi;
+        a.n_ang = nb;
+        a.partial = d_part;
+        a.s2 = d_s2;
+        a.amp = d_amp;
+        int l = 0;
+        CK(h, launch_far_field(a, h->stream, &l));
+        h->launches += l;
+        CK(h, cudaMemcpyAsync(s2 + b0, d_s2, nb * 8, cudaMemcpyDeviceToHost, h->stream));
+        if (amp)
+            CK(h, cudaMemcpyAsync(amp + (size_t)b0 * 12, d_amp, (size_t)nb * 12 * 8,
+                                  cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return LBEM_OK;
+}
+
+int32_t lbem_incident_amplitude(lbem_handle h, double *out)
+{
+    if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
+    int i0, i1;
+    centre_nodes(h, &i0, &i1);
+    double v[2][6];
+    CK(h, cudaMemcpyAsync(v[0], h->line_dft + (size_t)i0 * 6, 48, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(v[1], h->line_dft + (size_t)i1 * 6, 48, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    double ei = 0;
+    for (int t = 0; t < 2; ++t) {
+        double re = 0, im = 0;
+        for (int c = 0; c < 3; ++c) {
+            re += h->wave.pol[c] * v[t][2 * c];
+            im += h->wave.pol[c] * v[t][2 * c + 1];
+        }
+        ei += 0.5 * std::sqrt(re * re + im * im);
+    }
+    *out = ei;
+    return LBEM_OK;
+}
+
+int32_t lbem_get_populations(lbem_handle h, float *out, int32_t on_device)
+{
+    if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    for (int q = 0; q < h->Q; ++q) {
+        float *dst = on_device ? out + (size_t)q * h->ncell : h->stage;
+        CK(h, launch_pack(h->g.storage, h->f[h->cur], h->P, q, h->scale[q], dst, h->g.nx, h->g.ny,
+                          h->g.nz, h->nxp, h->stream));
+        h->launches += 1;
+        if (!on_device)
+            CK(h, cudaMemcpyAsync(out + (size_t)q * h->ncell, h->stage, (size_t)h->ncell * 4,
+                                  cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t on_device)
+{
+    if (!h || !in) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    for (int q = 0; q < h->Q; ++q) {
+        const float *src = in + (size_t)q * h->ncell;
+        if (!on_device) {
+            CK(h, cudaMemcpyAsync(h->stage, src, (size_t)h->ncell * 4, cudaMemcpyHostToDevice, h->stream));
+            src = h->stage;
+        }
+        CK(h, launch_unpack(h->g.storage, h->f[h->cur], h->P, q, h->inv_scale[q], src, h->g.nx,
+                            h->g.ny, h->g.nz, h->nxp, h->stream));
+        h->launches += 1;
+        if (!on_device) CK(h, cudaStreamSynchronize(h->stream));  // stage is reused
+    }
+    return LBEM_OK;
+}
+
+int32_t lbem_fields(lbem_handle h, float *E, float *H, int32_t on_device)
+{
+    if (!h || !E || !H) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    for (int comp = 0; comp < 6; ++comp) {
+        float *dst = (comp < 3 ? E : H) + (size_t)(comp % 3) * h->ncell;
+        float *out = on_device ? dst : h->stage;
+        CK(h, launch_fields(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->scale, h->P,
+                            h->g.nx, h->g.ny, h->g.nz, h->nxp, comp, out, h->stream));
+        h->launches += 1;
+        if (!on_device) {
+            CK(h, cudaMemcpyAsync(dst, h->stage, (size_t)h->ncell * 4, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+int32_t lbem_dft_doubles(lbem_handle h, size_t *count)
+{
+    if (!h || !count) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
+    *count = h->dft_doubles;
+    return LBEM_OK;
+}
+
+int32_t lbem_get_dft(lbem_handle h, double *out)
+{
+    if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
+    CK(h, cudaMemcpyAsync(out, h->dft, h->dft_doubles * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+int32_t lbem_energy(lbem_handle h, double *out)
+{
+    if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    double *d_out = h->scratch;
+    double *part = h->scratch + 8;
+    int l = 0;
+    CK(h, launch_energy(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->scale, h->P, h->g.nx,
+                        h->g.ny, h->g.nz, h->nxp, part, (int)(h->scratch_doubles - 8), d_out,
+                        h->stream, &l));
+    h->launches += l;
+    CK(h, cudaMemcpyAsync(out, d_out, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!std::isfinite(*out)) return fail(h, LBEM_ERR_NONFINITE, "non-finite population in the state");
+    return LBEM_OK;
+}
+
+// checkpoint: header | populations | incident line | line DFT | face DFT
+struct StateHeader {
+    char magic[8];
+    int32_t nx, ny, nz, mode, storage, Q;
+    int64_t t;
+    int64_t pop_bytes, line_bytes, line_dft_bytes, dft_bytes;
+};
+
+int32_t lbem_state_bytes(lbem_handle h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    *bytes = sizeof(StateHeader) + (size_t)h->Q * h->P * h->elem + (size_t)h->Q * h->n_line_max * 4 +
+             (size_t)h->n_line_max * 48 + h->dft_doubles_max * 8;
+    return LBEM_OK;
+}
+
+int32_t lbem_save_state(lbem_handle h, void *buf, size_t bytes)
+{
+    size_t need = 0;
+    if (!h || !buf) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    lbem_state_bytes(h, &need);
+    if (bytes < need) return fail(h, LBEM_ERR_ARG, "buffer of %zu bytes < %zu", bytes, need);
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, "LBEMSTA1", 8);
+    hd.nx = h->g.nx; hd.ny = h->g.ny; hd.nz = h->g.nz; hd.mode = h->g.mode; hd.storage = h->g.storage;
+    hd.Q = h->Q;
+    hd.t = h->t;
+    hd.pop_bytes = (int64_t)h->Q * h->P * h->elem;
+    hd.line_bytes = (int64_t)h->Q * h->n_line_max * 4;
+    hd.line_dft_bytes = (int64_t)h->n_line_max * 48;
+    hd.dft_bytes = (int64_t)h->dft_doubles_max * 8;
+    char *p = (char *)buf;
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    CK(h, cudaMemcpyAsync(p, h->f[h->cur], hd.pop_bytes, cudaMemcpyDeviceToHost, h->stream));
+    p += hd.pop_bytes;
+    CK(h, cudaMemcpyAsync(p, h->line[h->cur], hd.line_bytes, cudaMemcpyDeviceToHost, h->stream));
+    p += hd.line_bytes;
+    CK(h, cudaMemcpyAsync(p, h->line_dft, hd.line_dft_bytes, cudaMemcpyDeviceToHost, h->stream));
+    p += hd.line_dft_bytes;
+    CK(h, cudaMemcpyAsync(p, h->dft, hd.dft_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
+{
+    size_t need = 0;
+    if (!h || !buf) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    lbem_state_bytes(h, &need);
+    if (bytes < need) return fail(h, LBEM_ERR_ARG, "buffer of %zu bytes < %zu", bytes, need);
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (std::memcmp(hd.magic, "LBEMSTA1", 8) || hd.nx != h->g.nx || hd.ny != h->g.ny || hd.nz != h->g.nz ||
+        hd.mode != h->g.mode || hd.storage != h->g.storage || hd.Q != h->Q)
+        return fail(h, LBEM_ERR_ARG, "snapshot does not match this grid");
+    const char *p = (const char *)buf + sizeof hd;
+    CK(h, cudaMemcpyAsync(h->f[h->cur], p, hd.pop_bytes, cudaMemcpyHostToDevice, h->stream));
+    p += hd.pop_bytes;
+    CK(h, cudaMemcpyAsync(h->line[h->cur], p, hd.line_bytes, cudaMemcpyHostToDevice, h->stream));
+    p += hd.line_bytes;
+    CK(h, cudaMemcpyAsync(h->line_dft, p, hd.line_dft_bytes, cudaMemcpyHostToDevice, h->stream));
+    p += hd.line_dft_bytes;
+    CK(h, cudaMemcpyAsync(h->dft, p, hd.dft_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->t = hd.t;
+    return LBEM_OK;
+}
+
+int32_t lbem_set_storage_scales(lbem_handle h, const float *scales)
+{
+    if (!h || !scales) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    for (int q = 0; q < h->Q; ++q) {
+        int e;
+        const float m = std::frexp(scales[q], &e);
+        if (!(scales[q] > 0) || m != 0.5f) return fail(h, LBEM_ERR_ARG, "scale %d is not a power of two", q);
+    }
+    if (h->g.storage == LBEM_F32) return LBEM_OK;
+    for (int q = 0; q < h->Q; ++q) {
+        h->scale[q] = scales[q];
+        h->inv_scale[q] = 1.0f / scales[q];
+    }
+    return LBEM_OK;
+}
+
+int32_t lbem_get_storage_scales(lbem_handle h, float *scales)
+{
+    if (!h || !scales) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    for (int q = 0; q < h->Q; ++q) scales[q] = h->scale[q];
+    return LBEM_OK;
+}
+
+int32_t lbem_sync(lbem_handle h)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaGetLastError());
+    return LBEM_OK;
+}
+
+void lbem_destroy(lbem_handle h)
+{
+    if (!h) return;
+    if (h->owns_ws && h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+    }
+    delete h;
+}
+
+const char *lbem_last_error(lbem_handle h) { return h ? h->err : g_create_err; }
+
+int64_t lbem_kernel_launches(lbem_handle h) { return h ? h->launches : 0; }
+
+}  // extern "C"

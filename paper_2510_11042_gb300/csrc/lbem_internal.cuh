@@ -1,0 +1,135 @@
+// Internal definitions shared by the CUDA translation units of liblbem.
+// The public C ABI is include/lbem.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace lbem {
+
+constexpr int kMaxQ = 42;        // 2 families x 7 directions x 3 components (3D)
+constexpr int kMaxFaces = 6;
+constexpr int kAngleBatch = 1024;  // angles per far-field kernel pass
+constexpr int kMaxChunks = 64;     // face-cell chunks per angle in the projection
+
+// Per-mode population planes (Sec. 2.1, D3Q7 with 3-vector populations).  A
+// family stores only the vector components that are non-zero in the mode:
+//   mode 0 (EZ): e_z ; h_x h_y     mode 1 (HZ): e_x e_y ; h_z     mode 2 (3D): all
+// Plane q: e-planes q = i*NE + k, then h-planes q = 7*NE + i*NH + k.
+template <int MODE> struct Mode;
+template <> struct Mode<0> {
+    static constexpr int NE = 1, NH = 2;
+    __host__ __device__ static constexpr int ec(int) { return 2; }
+    __host__ __device__ static constexpr int hc(int k) { return k; }
+};
+template <> struct Mode<1> {
+    static constexpr int NE = 2, NH = 1;
+    __host__ __device__ static constexpr int ec(int k) { return k; }
+    __host__ __device__ static constexpr int hc(int) { return 2; }
+};
+template <> struct Mode<2> {
+    static constexpr int NE = 3, NH = 3;
+    __host__ __device__ static constexpr int ec(int k) { return k; }
+    __host__ __device__ static constexpr int hc(int k) { return k; }
+};
+template <int MODE> struct Planes {
+    using M = Mode<MODE>;
+    static constexpr int NE = M::NE, NH = M::NH;
+    static constexpr int Q = 7 * (NE + NH);
+    static constexpr int NC = NE + NH;  // field components recorded by the DFT
+    __host__ __device__ static constexpr int dir(int q) { return q < 7 * NE ? q / NE : (q - 7 * NE) / NH; }
+    __host__ __device__ static constexpr int fam(int q) { return q < 7 * NE ? 0 : 1; }
+    __host__ __device__ static constexpr int comp(int q) {
+        return q < 7 * NE ? M::ec(q % NE) : M::hc((q - 7 * NE) % NH);
+    }
+};
+
+inline int planes_of_mode(int mode) { return mode == 2 ? 42 : 21; }
+inline int dft_comps_of_mode(int mode) { return mode == 2 ? 6 : 3; }
+
+// Arguments of the fused step kernel (passed by value).
+struct StepArgs {
+    const void *fin;
+    void *fout;
+    const float *inv_eps;
+    int nx, ny, nz, nxp;       // extent and padded row pitch (elements)
+    long long P;               // plane stride in elements = nz*ny*nxp
+    int nblk_x;                // blocks per row
+    int nblk_main;             // blocks covering the lattice
+    // absorbing layer
+    int w;
+    float sigma_max, inv_w;
+    // TF/SF source
+    int tfsf;
+    int tf_lo[3], tf_hi[3];
+    int inc_axis;
+    const float *inc;          // incident line at time n: [Q][n_line]
+    int n_line;
+    // DFT of the near fields on the NTFF box surface
+    int dft_on;
+    double dft_c, dft_s, dft_scale;
+    int nt_lo[3], nt_hi[3];
+    double *dft;
+    long long face_off[kMaxFaces];
+    int face_nu[kMaxFaces], face_nv[kMaxFaces];
+    // incident line update (executed by one extra block)
+    int line_on;
+    const float *line_in;
+    float *line_out;
+    int src_index;
+    float src_E[3], src_H[3];
+    double *line_dft;          // [n_line][3][2]
+    // reduced-precision storage scales
+    float scale[kMaxQ], inv_scale[kMaxQ];
+};
+
+// Launchers (step.cu)
+cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
+
+// Observables and data movement (observe.cu)
+struct FaceGeom {
+    int nfaces;
+    int axis[kMaxFaces], side[kMaxFaces];
+    int nu[kMaxFaces], nv[kMaxFaces];
+    long long off[kMaxFaces];  // offset in doubles of face f in the DFT array
+    long long cell_start[kMaxFaces + 1];  // prefix sum of nu*nv
+    int lo[3], hi[3];
+};
+
+struct FarFieldArgs {
+    const double *dft;
+    const double *line_dft;
+    FaceGeom g;
+    int mode;
+    int n_ang;
+    const double *theta, *phi;
+    double k;
+    double center[3];
+    double pol[3];
+    int center_i0, center_i1;  // incident-line nodes bracketing the centre
+    int chunks;
+    double *partial;           // [n_ang][chunks][12]
+    double *s2;                // [n_ang]
+    double *amp;               // [n_ang][12]
+};
+cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launches);
+
+cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int nz, int nxp,
+                           int *bad_flag, cudaStream_t s);
+cudaError_t launch_pack(int storage, const void *f, long long P, int q, float scale, float *out,
+                        int nx, int ny, int nz, int nxp, cudaStream_t s);
+cudaError_t launch_unpack(int storage, void *f, long long P, int q, float inv_scale,
+                          const float *in, int nx, int ny, int nz, int nxp, cudaStream_t s);
+cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps,
+                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
+                          int comp, float *out, cudaStream_t s);
+cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps,
+                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
+                          double *partial, int max_partial, double *out, cudaStream_t s,
+                          int *launches);
+
+}  // namespace lbem

@@ -1,0 +1,410 @@
+// Observables and data movement of liblbem:
+//   * the FP64 near-to-far-field projection (Sec. 2.4, Eqs. 7-10 in the
+//     far-field limit) and the angular intensity |S|^2 (Sec. 2.3, Eqs. 5-6);
+//   * the field-energy monitor (Sec. 3.2: steady state is checked by the total
+//     field energy) with its non-finite check;
+//   * fields of the stored state, permittivity upload, population pack/unpack.
+#include <type_traits>
+
+#include "lbem_internal.cuh"
+
+namespace lbem {
+namespace {
+
+template <class S> __device__ __forceinline__ float ldv(const S *p);
+template <> __device__ __forceinline__ float ldv<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float ldv<__half>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(*p);
+}
+template <class S> __device__ __forceinline__ void stv(S *p, float v);
+template <> __device__ __forceinline__ void stv<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void stv<__half>(__half *p, float v) { *p = __float2half_rn(v); }
+template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------ far field
+// Stage 1: one block per (chunk, angle) sums w J e^{j phi}, w M e^{j phi} over
+// its share of the face cells; writes 12 doubles (Re/Im of N_xyz, L_xyz).
+constexpr int kFFThreads = 256;
+
+__global__ void __launch_bounds__(kFFThreads) far_field_partial(const FarFieldArgs a)
+{
+    const int ang = blockIdx.y;
+    const int chunk = blockIdx.x;
+    const double th = a.theta[ang];
+    double rh[3];
+    if (a.mode == 2) {
+        const double ph = a.phi[ang];
+        rh[0] = sin(th) * cos(ph);
+        rh[1] = sin(th) * sin(ph);
+        rh[2] = cos(th);
+    } else {
+        rh[0] = cos(th);
+        rh[1] = sin(th);
+        rh[2] = 0.0;
+    }
+    const int NE = a.mode == 0 ? 1 : (a.mode == 1 ? 2 : 3);
+    const int NC = a.mode == 2 ? 6 : 3;
+    const long long total = a.g.cell_start[a.g.nfaces];
+    const long long per = (total + a.chunks - 1) / a.chunks;
+    const long long j0 = (long long)chunk * per;
+    const long long j1 = min(total, j0 + per);
+
+    double acc[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) acc[m] = 0.0;
+
+    for (long long j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        int f = 0;
+        while (f + 1 < a.g.nfaces && j >= a.g.cell_start[f + 1]) ++f;
+        const long long jl = j - a.g.cell_start[f];
+        const int nu = a.g.nu[f], nv = a.g.nv[f];
+        const int iu = (int)(jl / nv), iv = (int)(jl % nv);
+        const int ax = a.g.axis[f];
+        const int ua = ax == 2 ? 1 : 2, va = ax == 0 ? 1 : 0;
+        double pos[3];
+        pos[ax] = a.g.side[f] ? a.g.hi[ax] : a.g.lo[ax];
+        pos[ua] = a.g.lo[ua] + iu;
+        pos[va] = a.g.lo[va] + iv;
+        // trapezoidal weights: 1/2 on the edges of each face
+        double w = 1.0;
+        if (nu > 1 && (iu == 0 || iu == nu - 1)) w *= 0.5;
+        if (nv > 1 && (iv == 0 || iv == nv - 1)) w *= 0.5;
+        const double phase = a.k * (rh[0] * (pos[0] - a.center[0]) + rh[1] * (pos[1] - a.center[1]) +
+                                    rh[2] * (pos[2] - a.center[2]));
+        double sp, cp;
+        sincos(phase, &sp, &cp);
+        // field phasors of this face cell
+        const double *base = a.dft + a.g.off[f] + jl;
+        const long long plane = (long long)nu * nv;
+        double Er[3] = {0, 0, 0}, Ei[3] = {0, 0, 0}, Hr[3] = {0, 0, 0}, Hi[3] = {0, 0, 0};
+        for (int k = 0; k < NC; ++k) {
+            const double re = base[(2 * k) * plane], im = base[(2 * k + 1) * plane];
+            int comp;
+            bool isE;
+            if (a.mode == 0) { isE = k < 1; comp = isE ? 2 : k - 1; }
+            else if (a.mode == 1) { isE = k < 2; comp = isE ? k : 2; }
+            else { isE = k < NE; comp = isE ? k : k - 3; }
+            if (isE) { Er[comp] = re; Ei[comp] = im; }
+            else { Hr[comp] = re; Hi[comp] = im; }
+        }
+        // n = side ? +e_ax : -e_ax;  J = n x H, M = -n x E
+        const double sgn = a.g.side[f] ? 1.0 : -1.0;
+        double Jr[3], Ji[3], Mr[3], Mi[3];
+        const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+        // (e_ax x V)_b1 = -V_b2, (e_ax x V)_b2 = V_b1, (e_ax x V)_ax = 0
+        Jr[ax] = 0; Ji[ax] = 0; Mr[ax] = 0; Mi[ax] = 0;
+        Jr[b1] = -sgn * Hr[b2]; Ji[b1] = -sgn * Hi[b2];
+        Jr[b2] = sgn * Hr[b1];  Ji[b2] = sgn * Hi[b1];
+        Mr[b1] = sgn * Er[b2];  Mi[b1] = sgn * Ei[b2];
+        Mr[b2] = -sgn * Er[b1]; Mi[b2] = -sgn * Ei[b1];
+        const double wc = w * cp, ws = w * sp;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[2 * c + 0] += Jr[c] * wc - Ji[c] * ws;
+            acc[2 * c + 1] += Jr[c] * ws + Ji[c] * wc;
+            acc[6 + 2 * c + 0] += Mr[c] * wc - Mi[c] * ws;
+            acc[6 + 2 * c + 1] += Mr[c] * ws + Mi[c] * wc;
+        }
+    }
+
+    __shared__ double red[kFFThreads / 32][12];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+        const double v = warp_sum(acc[m]);
+        if (lane == 0) red[wid][m] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        double s = 0.0;
+        for (int wi = 0; wi < kFFThreads / 32; ++wi) s += red[wi][threadIdx.x];
+        a.partial[((long long)ang * a.chunks + chunk) * 12 + threadIdx.x] = s;
+    }
+}
+
+// Stage 2: one thread per angle; fixed-order sum over chunks, then Eq. 5/6.
+__global__ void far_field_finalize(const FarFieldArgs a)
+{
+    const int ang = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ang >= a.n_ang) return;
+    double v[12];
+    for (int m = 0; m < 12; ++m) v[m] = 0.0;
+    for (int c = 0; c < a.chunks; ++c)
+        for (int m = 0; m < 12; ++m) v[m] += a.partial[((long long)ang * a.chunks + c) * 12 + m];
+    // |E_I|: incident-line E phasor along pol, mean over the two nodes around the centre
+    double ei = 0.0;
+    const int nodes[2] = {a.center_i0, a.center_i1};
+    for (int t = 0; t < 2; ++t) {
+        double re = 0.0, im = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            re += a.pol[c] * a.line_dft[(nodes[t] * 3 + c) * 2 + 0];
+            im += a.pol[c] * a.line_dft[(nodes[t] * 3 + c) * 2 + 1];
+        }
+        ei += 0.5 * sqrt(re * re + im * im);
+    }
+    const double th = a.theta[ang];
+    const double k = a.k;
+    double s2;
+    if (a.mode == 2) {
+        const double ph = a.phi[ang];
+        const double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
+        const double tv[3] = {ct * cp, ct * sp, -st}, pv[3] = {-sp, cp, 0.0};
+        double Nt[2] = {0, 0}, Np[2] = {0, 0}, Lt[2] = {0, 0}, Lp[2] = {0, 0};
+        for (int c = 0; c < 3; ++c)
+            for (int r = 0; r < 2; ++r) {
+                Nt[r] += tv[c] * v[2 * c + r];
+                Np[r] += pv[c] * v[2 * c + r];
+                Lt[r] += tv[c] * v[6 + 2 * c + r];
+                Lp[r] += pv[c] * v[6 + 2 * c + r];
+            }
+        const double a1r = Nt[0] + Lp[0], a1i = Nt[1] + Lp[1];
+        const double a2r = Np[0] - Lt[0], a2i = Np[1] - Lt[1];
+        s2 = k * k * k * k * (a1r * a1r + a1i * a1i + a2r * a2r + a2i * a2i) /
+             (16.0 * M_PI * M_PI * ei * ei);
+    } else {
+        const double pv[3] = {-sin(th), cos(th), 0.0};
+        double Np[2] = {0, 0}, Lp[2] = {0, 0};
+        for (int c = 0; c < 3; ++c)
+            for (int r = 0; r < 2; ++r) {
+                Np[r] += pv[c] * v[2 * c + r];
+                Lp[r] += pv[c] * v[6 + 2 * c + r];
+            }
+        double ar, ai;
+        if (a.mode == 0) { ar = v[4] - Lp[0]; ai = v[5] - Lp[1]; }      // N_z - L_phi
+        else { ar = Np[0] + v[10]; ai = Np[1] + v[11]; }                // N_phi + L_z
+        s2 = k * k * (ar * ar + ai * ai) / (8.0 * M_PI * ei * ei);
+    }
+    a.s2[ang] = s2;
+    if (a.amp)
+        for (int m = 0; m < 12; ++m) a.amp[(long long)ang * 12 + m] = v[m];
+}
+
+// ------------------------------------------------------------ permittivity
+// inv_eps == nullptr: only validate (eps_r finite and >= 1) into *bad.
+__global__ void inv_eps_kernel(const float *eps, float *inv_eps, int nx, int ny, int nz, int nxp,
+                               int *bad)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long r = i / nx;
+        const float e = eps[i];
+        if (inv_eps == nullptr) {
+            if (!(e >= 1.0f) || !isfinite(e)) atomicOr(bad, 1);
+        } else {
+            inv_eps[r * nxp + x] = 1.0f / e;
+        }
+    }
+}
+
+// ------------------------------------------------------------ pack / unpack
+template <class S>
+__global__ void pack_kernel(const S *f, float scale, float *out, int nx, long long ncell, int nxp)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long r = i / nx;
+        out[i] = ldv<S>(f + r * nxp + x) * scale;
+    }
+}
+
+template <class S>
+__global__ void unpack_kernel(S *f, float inv_scale, const float *in, int nx, long long ncell, int nxp)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long r = i / nx;
+        stv<S>(f + r * nxp + x, in[i] * inv_scale);
+    }
+}
+
+// ------------------------------------------------------------ fields & energy
+struct ScaleTab { float s[kMaxQ]; };
+
+template <int MODE, class S>
+__device__ __forceinline__ void cell_DB(const S *f, const ScaleTab &sc, long long P, long long c,
+                                        float D[3], float B[3])
+{
+    using PL = Planes<MODE>;
+    D[0] = D[1] = D[2] = 0.f;
+    B[0] = B[1] = B[2] = 0.f;
+#pragma unroll
+    for (int q = 0; q < PL::Q; ++q) {
+        const float v = ldv<S>(f + q * P + c) * sc.s[q];
+        if (PL::fam(q) == 0) D[PL::comp(q)] += v;
+        else B[PL::comp(q)] += v;
+    }
+}
+
+// One field component per launch: comp 0..2 -> E_x..E_z, 3..5 -> H_x..H_z.
+template <int MODE, class S>
+__global__ void fields_kernel(const S *f, const float *inv_eps, ScaleTab sc, long long P, int nx,
+                              long long ncell, int nxp, int comp, float *out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long c = (i / nx) * nxp + x;
+        float D[3], B[3];
+        cell_DB<MODE, S>(f, sc, P, c, D, B);
+        out[i] = comp < 3 ? D[comp] * inv_eps[c] : B[comp - 3];
+    }
+}
+
+constexpr int kEThreads = 256;
+
+template <int MODE, class S>
+__global__ void __launch_bounds__(kEThreads) energy_partial(const S *f, const float *inv_eps,
+                                                            ScaleTab sc, long long P, int nx,
+                                                            long long ncell, int nxp, double *partial)
+{
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long c = (i / nx) * nxp + x;
+        float D[3], B[3];
+        cell_DB<MODE, S>(f, sc, P, c, D, B);
+        const double ie = inv_eps[c];
+        // 1/2 (eps |E|^2 + |H|^2) = 1/2 (|D|^2 / eps + |B|^2)
+        acc += 0.5 * (((double)D[0] * D[0] + (double)D[1] * D[1] + (double)D[2] * D[2]) * ie +
+                      (double)B[0] * B[0] + (double)B[1] * B[1] + (double)B[2] * B[2]);
+    }
+    __shared__ double red[kEThreads / 32];
+    const double v = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kEThreads / 32; ++w) s += red[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void sum_partials(const double *partial, int n, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += partial[i];
+        *out = s;
+    }
+}
+
+inline int grid_for(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launches)
+{
+    dim3 g1(a.chunks, a.n_ang);
+    far_field_partial<<<g1, kFFThreads, 0, s>>>(a);
+    far_field_finalize<<<(a.n_ang + 127) / 128, 128, 0, s>>>(a);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int nz, int nxp,
+                           int *bad_flag, cudaStream_t s)
+{
+    const long long n = (long long)nx * ny * nz;
+    inv_eps_kernel<<<grid_for(n, 256), 256, 0, s>>>(eps, inv_eps, nx, ny, nz, nxp, bad_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int storage, const void *f, long long P, int q, float scale, float *out,
+                        int nx, int ny, int nz, int nxp, cudaStream_t s)
+{
+    const long long n = (long long)nx * ny * nz;
+    const int g = grid_for(n, 256);
+    if (storage == 0) pack_kernel<float><<<g, 256, 0, s>>>((const float *)f + q * P, scale, out, nx, n, nxp);
+    else if (storage == 1) pack_kernel<__half><<<g, 256, 0, s>>>((const __half *)f + q * P, scale, out, nx, n, nxp);
+    else pack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16 *)f + q * P, scale, out, nx, n, nxp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int storage, void *f, long long P, int q, float inv_scale,
+                          const float *in, int nx, int ny, int nz, int nxp, cudaStream_t s)
+{
+    const long long n = (long long)nx * ny * nz;
+    const int g = grid_for(n, 256);
+    if (storage == 0) unpack_kernel<float><<<g, 256, 0, s>>>((float *)f + q * P, inv_scale, in, nx, n, nxp);
+    else if (storage == 1) unpack_kernel<__half><<<g, 256, 0, s>>>((__half *)f + q * P, inv_scale, in, nx, n, nxp);
+    else unpack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)f + q * P, inv_scale, in, nx, n, nxp);
+    return cudaGetLastError();
+}
+
+template <int MODE, class S>
+static cudaError_t fields_t(const void *f, const float *inv_eps, const float *scale, long long P,
+                            int nx, int ny, int nz, int nxp, int comp, float *out, cudaStream_t s)
+{
+    ScaleTab sc;
+    for (int q = 0; q < kMaxQ; ++q) sc.s[q] = scale[q];
+    const long long n = (long long)nx * ny * nz;
+    fields_kernel<MODE, S><<<grid_for(n, 256), 256, 0, s>>>((const S *)f, inv_eps, sc, P, nx, n, nxp,
+                                                             comp, out);
+    return cudaGetLastError();
+}
+
+template <int MODE, class S>
+static cudaError_t energy_t(const void *f, const float *inv_eps, const float *scale, long long P,
+                            int nx, int ny, int nz, int nxp, double *partial, int max_partial,
+                            double *out, cudaStream_t s)
+{
+    ScaleTab sc;
+    for (int q = 0; q < kMaxQ; ++q) sc.s[q] = scale[q];
+    const long long n = (long long)nx * ny * nz;
+    int g = grid_for(n, kEThreads);
+    if (g > max_partial) g = max_partial;
+    energy_partial<MODE, S><<<g, kEThreads, 0, s>>>((const S *)f, inv_eps, sc, P, nx, n, nxp, partial);
+    sum_partials<<<1, 32, 0, s>>>(partial, g, out);
+    return cudaGetLastError();
+}
+
+#define LBEM_DISPATCH(FN, ...)                                                   \
+    switch (mode * 3 + storage) {                                                \
+    case 0: return FN<0, float>(__VA_ARGS__);                                    \
+    case 1: return FN<0, __half>(__VA_ARGS__);                                   \
+    case 2: return FN<0, __nv_bfloat16>(__VA_ARGS__);                            \
+    case 3: return FN<1, float>(__VA_ARGS__);                                    \
+    case 4: return FN<1, __half>(__VA_ARGS__);                                   \
+    case 5: return FN<1, __nv_bfloat16>(__VA_ARGS__);                            \
+    case 6: return FN<2, float>(__VA_ARGS__);                                    \
+    case 7: return FN<2, __half>(__VA_ARGS__);                                   \
+    case 8: return FN<2, __nv_bfloat16>(__VA_ARGS__);                            \
+    default: return cudaErrorInvalidValue;                                       \
+    }
+
+cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps,
+                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
+                          int comp, float *out, cudaStream_t s)
+{
+    LBEM_DISPATCH(fields_t, f, inv_eps, scale, P, nx, ny, nz, nxp, comp, out, s)
+}
+
+cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps,
+                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
+                          double *partial, int max_partial, double *out, cudaStream_t s,
+                          int *launches)
+{
+    if (launches) *launches += 2;
+    LBEM_DISPATCH(energy_t, f, inv_eps, scale, P, nx, ny, nz, nxp, partial, max_partial, out, s)
+}
+
+}  // namespace lbem

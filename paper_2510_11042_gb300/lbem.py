@@ -1,0 +1,402 @@
+"""Thin ctypes binding of liblbem (include/lbem.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions carry the C names; ``Solver`` bundles them with a torch-allocated
+device workspace and torch's current CUDA stream.  There is no CPU fallback:
+loading fails loudly when the library cannot be found or built.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+LBEM_OK = 0
+LBEM_ERR_ARG = -1
+LBEM_ERR_OOM = -2
+LBEM_ERR_CUDA = -3
+LBEM_ERR_NONFINITE = -4
+LBEM_ERR_TIMEOUT = -5
+LBEM_ERR_STATE = -6
+
+LBEM_D3Q7 = 0
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+MODE = {"ez": 0, "hz": 1, "3d": 2}
+
+
+class LbemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lbem error %d: %s" % (code, msg))
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("absorber_width", ctypes.c_int32), ("sigma_max", ctypes.c_double),
+                ("storage", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+class PlaneWaveDesc(ctypes.Structure):
+    _fields_ = [("dir", ctypes.c_double * 3), ("pol", ctypes.c_double * 3),
+                ("wavelength", ctypes.c_double), ("amplitude", ctypes.c_double),
+                ("ramp_periods", ctypes.c_double),
+                ("tfsf_lo", ctypes.c_int32 * 3), ("tfsf_hi", ctypes.c_int32 * 3),
+                ("ntff_lo", ctypes.c_int32 * 3), ("ntff_hi", ctypes.c_int32 * 3),
+                ("center", ctypes.c_double * 3), ("source_index", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_SIGS = {
+    "lbem_workspace_bytes": (_I32, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_size_t)]),
+    "lbem_create": (_I32, [ctypes.POINTER(GridDesc), _I32, _P, _I32, _P, _P, ctypes.c_size_t,
+                           ctypes.POINTER(_P)]),
+    "lbem_set_permittivity": (_I32, [_P, _P, _I32]),
+    "lbem_inject_plane_wave": (_I32, [_P, ctypes.POINTER(PlaneWaveDesc)]),
+    "lbem_set_dft_window": (_I32, [_P, _I64, _I32]),
+    "lbem_step": (_I32, [_P, _I64]),
+    "lbem_get_time": (_I32, [_P, ctypes.POINTER(_I64)]),
+    "lbem_far_field": (_I32, [_P, _P, _P, _I32, _P, _P]),
+    "lbem_incident_amplitude": (_I32, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "lbem_get_populations": (_I32, [_P, _P, _I32]),
+    "lbem_set_populations": (_I32, [_P, _P, _I32]),
+    "lbem_fields": (_I32, [_P, _P, _P, _I32]),
+    "lbem_dft_doubles": (_I32, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbem_get_dft": (_I32, [_P, _P]),
+    "lbem_energy": (_I32, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "lbem_state_bytes": (_I32, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbem_save_state": (_I32, [_P, _P, ctypes.c_size_t]),
+    "lbem_load_state": (_I32, [_P, _P, ctypes.c_size_t]),
+    "lbem_set_storage_scales": (_I32, [_P, _P]),
+    "lbem_get_storage_scales": (_I32, [_P, _P]),
+    "lbem_sync": (_I32, [_P]),
+    "lbem_destroy": (None, [_P]),
+    "lbem_last_error": (ctypes.c_char_p, [_P]),
+    "lbem_kernel_launches": (_I64, [_P]),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load liblbem.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError("liblbem.so is missing and could not be built")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, h=None):
+    if rc != LBEM_OK:
+        msg = lib().lbem_last_error(h)
+        raise LbemError(rc, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor or numpy array, and whether it is on a GPU."""
+    if x is None:
+        return None, 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), int(x.is_cuda)
+    if not x.flags.c_contiguous:
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data, 0
+
+
+def grid_desc(nx, ny, nz, mode="3d", storage="f32", absorber_width=0, sigma_max=0.3) -> GridDesc:
+    return GridDesc(nx, ny, nz, absorber_width, sigma_max, STORAGE[storage], MODE[mode])
+
+
+def plane_wave_desc(wave) -> PlaneWaveDesc:
+    """From a workloads.PlaneWave (or any object with the same attributes)."""
+    d = PlaneWaveDesc()
+    d.dir[:] = wave.direction
+    d.pol[:] = wave.polarization
+    d.wavelength = wave.wavelength
+    d.amplitude = wave.amplitude
+    d.ramp_periods = wave.ramp_periods
+    d.tfsf_lo[:] = wave.tf_lo
+    d.tfsf_hi[:] = wave.tf_hi
+    d.ntff_lo[:] = wave.ntff_lo
+    d.ntff_hi[:] = wave.ntff_hi
+    d.center[:] = wave.center
+    d.source_index = wave.source_index
+    return d
+
+
+# ------------------------------------------------------------ C-named wrappers
+def lbem_workspace_bytes(grid: GridDesc) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().lbem_workspace_bytes(ctypes.byref(grid), ctypes.byref(n)))
+    return n.value
+
+
+def lbem_create(grid: GridDesc, eps_r, stream=None, workspace=None) -> int:
+    """eps_r: float32 [nz][ny][nx] numpy array (host) or torch CUDA tensor.
+    workspace: torch uint8 CUDA tensor of lbem_workspace_bytes() or None."""
+    ep, on_dev = _ptr(eps_r)
+    wp, _ = _ptr(workspace)
+    wbytes = workspace.numel() if workspace is not None else 0
+    h = ctypes.c_void_p()
+    _check(lib().lbem_create(ctypes.byref(grid), LBEM_D3Q7, ep, on_dev, stream, wp, wbytes,
+                             ctypes.byref(h)))
+    return h.value
+
+
+def lbem_set_permittivity(h, eps_r):
+    ep, on_dev = _ptr(eps_r)
+    _check(lib().lbem_set_permittivity(h, ep, on_dev), h)
+
+
+def lbem_inject_plane_wave(h, wave: PlaneWaveDesc):
+    _check(lib().lbem_inject_plane_wave(h, ctypes.byref(wave)), h)
+
+
+def lbem_set_dft_window(h, t_start: int, n_periods: int):
+    _check(lib().lbem_set_dft_window(h, int(t_start), int(n_periods)), h)
+
+
+def lbem_step(h, n: int):
+    _check(lib().lbem_step(h, int(n)), h)
+
+
+def lbem_get_time(h) -> int:
+    t = _I64()
+    _check(lib().lbem_get_time(h, ctypes.byref(t)), h)
+    return t.value
+
+
+def lbem_far_field(h, theta, phi=None, with_amplitudes=False):
+    theta = np.ascontiguousarray(theta, np.float64)
+    phi_a = None if phi is None else np.ascontiguousarray(phi, np.float64)
+    n = theta.size
+    s2 = np.empty(n)
+    amp = np.empty((n, 12)) if with_amplitudes else None
+    _check(lib().lbem_far_field(h, theta.ctypes.data,
+                                None if phi_a is None else phi_a.ctypes.data, n, s2.ctypes.data,
+                                None if amp is None else amp.ctypes.data), h)
+    return (s2, amp) if with_amplitudes else s2
+
+
+def lbem_incident_amplitude(h) -> float:
+    v = ctypes.c_double()
+    _check(lib().lbem_incident_amplitude(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def lbem_get_populations(h, out):
+    p, on_dev = _ptr(out)
+    _check(lib().lbem_get_populations(h, p, on_dev), h)
+    return out
+
+
+def lbem_set_populations(h, arr):
+    p, on_dev = _ptr(arr)
+    _check(lib().lbem_set_populations(h, p, on_dev), h)
+
+
+def lbem_fields(h, E_out, H_out):
+    pe, on_dev = _ptr(E_out)
+    ph, on_dev2 = _ptr(H_out)
+    if on_dev != on_dev2:
+        raise ValueError("E_out and H_out must both be host or both be device memory")
+    _check(lib().lbem_fields(h, pe, ph, on_dev), h)
+    return E_out, H_out
+
+
+def lbem_dft_doubles(h) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().lbem_dft_doubles(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def lbem_get_dft(h) -> np.ndarray:
+    out = np.empty(lbem_dft_doubles(h))
+    _check(lib().lbem_get_dft(h, out.ctypes.data), h)
+    return out
+
+
+def lbem_energy(h) -> float:
+    v = ctypes.c_double()
+    _check(lib().lbem_energy(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def lbem_state_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().lbem_state_bytes(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def lbem_save_state(h) -> np.ndarray:
+    buf = np.empty(lbem_state_bytes(h), np.uint8)
+    _check(lib().lbem_save_state(h, buf.ctypes.data, buf.size), h)
+    return buf
+
+
+def lbem_load_state(h, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, np.uint8)
+    _check(lib().lbem_load_state(h, buf.ctypes.data, buf.size), h)
+
+
+def lbem_set_storage_scales(h, scales):
+    s = np.ascontiguousarray(scales, np.float32)
+    _check(lib().lbem_set_storage_scales(h, s.ctypes.data), h)
+
+
+def lbem_get_storage_scales(h, q: int) -> np.ndarray:
+    s = np.zeros(42, np.float32)
+    _check(lib().lbem_get_storage_scales(h, s.ctypes.data), h)
+    return s[:q]
+
+
+def lbem_sync(h):
+    _check(lib().lbem_sync(h), h)
+
+
+def lbem_destroy(h):
+    lib().lbem_destroy(h)
+
+
+def lbem_last_error(h=None) -> str:
+    m = lib().lbem_last_error(h)
+    return m.decode() if m else ""
+
+
+def lbem_kernel_launches(h) -> int:
+    return int(lib().lbem_kernel_launches(h))
+
+
+# ------------------------------------------------------------ convenience object
+def n_planes(mode: str) -> int:
+    return 42 if mode == "3d" else 21
+
+
+class Solver:
+    """One lattice on the current CUDA device, workspace owned by torch."""
+
+    def __init__(self, shape, eps, mode="3d", storage="f32", absorber_width=0, sigma_max=0.3,
+                 device=None):
+        import torch
+        self.torch = torch
+        nx, ny, nz = shape
+        self.shape = (nx, ny, nz)
+        self.mode = mode
+        self.storage = storage
+        self.Q = n_planes(mode)
+        self.grid = grid_desc(nx, ny, nz, mode, storage, absorber_width, sigma_max)
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        with torch.cuda.device(dev):
+            nbytes = lbem_workspace_bytes(self.grid)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            self.stream = torch.cuda.current_stream(dev)
+            eps_arr = eps if hasattr(eps, "data_ptr") else np.ascontiguousarray(eps, np.float32)
+            self.h = lbem_create(self.grid, eps_arr, self.stream.cuda_stream, self.workspace)
+        self.wave = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # thin forwards
+    def inject(self, wave):
+        self.wave = wave
+        lbem_inject_plane_wave(self.h, plane_wave_desc(wave))
+
+    def set_dft_window(self, t_start, n_periods=1):
+        lbem_set_dft_window(self.h, t_start, n_periods)
+
+    def step(self, n):
+        lbem_step(self.h, n)
+
+    @property
+    def time(self):
+        return lbem_get_time(self.h)
+
+    def far_field(self, theta, phi=None, with_amplitudes=False):
+        return lbem_far_field(self.h, theta, phi, with_amplitudes)
+
+    def incident_amplitude(self):
+        return lbem_incident_amplitude(self.h)
+
+    def populations(self):
+        nx, ny, nz = self.shape
+        out = np.empty((self.Q, nz, ny, nx), np.float32)
+        return lbem_get_populations(self.h, out)
+
+    def set_populations(self, arr):
+        lbem_set_populations(self.h, np.ascontiguousarray(arr, np.float32))
+
+    def fields(self):
+        nx, ny, nz = self.shape
+        E = np.empty((3, nz, ny, nx), np.float32)
+        H = np.empty((3, nz, ny, nx), np.float32)
+        return lbem_fields(self.h, E, H)
+
+    def dft(self):
+        return lbem_get_dft(self.h)
+
+    def energy(self):
+        return lbem_energy(self.h)
+
+    def sync(self):
+        lbem_sync(self.h)
+
+    def kernel_launches(self):
+        return lbem_kernel_launches(self.h)
+
+
+def dft_faces(flat: np.ndarray, mode: str, shape, ntff_lo, ntff_hi):
+    """Split the flat face-DFT array into per-face complex arrays
+    [C][nu][nv] with the layout documented in lbem.h."""
+    nx, ny, nz = shape
+    n3 = (nx, ny, nz)
+    C = 6 if mode == "3d" else 3
+    faces = []
+    off = 0
+    for ax in range(3):
+        if n3[ax] <= 1:
+            continue
+        ua = 1 if ax == 2 else 2
+        va = 1 if ax == 0 else 0
+        nu = ntff_hi[ua] - ntff_lo[ua] + 1
+        nv = ntff_hi[va] - ntff_lo[va] + 1
+        for side in (0, 1):
+            blk = flat[off:off + C * 2 * nu * nv].reshape(C, 2, nu, nv)
+            faces.append(dict(axis=ax, side=side, ua=ua, va=va, data=blk[:, 0] + 1j * blk[:, 1]))
+            off += C * 2 * nu * nv
+    return faces

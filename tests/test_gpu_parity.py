@@ -1,0 +1,194 @@
+"""GPU <-> oracle parity through the C ABI (needs a GB300).
+
+Bar: relative L2 <= 1e-5 for FP32 storage on populations, DFT phasors and the
+far-field intensity, against the FP64 oracle on the same seeded inputs.
+FP16/BF16 storage errors are reported and checked against looser bounds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from _parity import (angles, gpu_solver, oracle_faces, oracle_run, oracle_to_planes,
+                     planes_to_oracle, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_11042_gb300 import lbem
+    lbem.lib()
+
+
+def random_problem(mode, shape, seed=1234, steps=200, lam=8.0, w=6):
+    """Seeded random problem: eps ~ U[1, 6], a plane wave with TF/SF and DFT."""
+    eps = W.random_eps(shape, 1.0, 6.0, seed)
+    wave = W.axis_wave(mode, shape, w, lam, gap_ntff=2, gap_tf=3)
+    # vacuum on the TF/SF and NTFF surfaces (the source lives in vacuum)
+    nx, ny, nz = shape
+    lo, hi = wave.ntff_lo, wave.ntff_hi
+    mask = np.ones((nz, ny, nx), bool)
+    sl = [slice(None)] * 3
+    inner = [slice(lo[2] + 4, hi[2] - 3) if nz > 1 else slice(None),
+             slice(lo[1] + 4, hi[1] - 3), slice(lo[0] + 4, hi[0] - 3)]
+    mask[tuple(inner)] = False
+    eps[mask] = 1.0
+    return W.Problem(f"random_{mode}", mode, shape, eps, w, 0.3, wave, steps, 1)
+
+
+@pytest.mark.parametrize("mode,shape", [("ez", (96, 80, 1)), ("hz", (96, 80, 1)),
+                                        ("3d", (40, 36, 28))])
+def test_random_state_parity_fp32(mode, shape):
+    p = random_problem(mode, shape)
+    init = W.random_state(mode, shape, 1234)
+    from oracle import lb
+    s = gpu_solver(p, init=init, steps=0)
+    r = lb.Run(p)
+    r.main.f = planes_to_oracle(init.astype(np.float64), mode)
+    done = 0
+    for n in (1, 2, 17, 200):
+        s.step(n - done)
+        r.step(n - done)
+        done = n
+        err = rel_l2(s.populations(), oracle_to_planes(r.main.f, mode, shape))
+        assert err <= TOL, (n, err)
+    # DFT phasors on the NTFF faces and the far field
+    from paper_2510_11042_gb300 import lbem
+    faces = lbem.dft_faces(s.dft(), mode, shape, p.wave.ntff_lo, p.wave.ntff_hi)
+    ref = oracle_faces(r.phasors(), mode, p.wave.ntff_lo, p.wave.ntff_hi)
+    got = np.concatenate([f["data"].ravel() for f in faces])
+    exp = np.concatenate([f.ravel() for f in ref])
+    assert got.shape == exp.shape
+    # A phasor X = 2/T sum_t x(t) e^{-jwt} obeys |dX| <= 2 max_t |dx(t)|, so its error
+    # is bounded by the field error times the field scale.  Broadband random states
+    # give phasors well below that scale, so normalise by the larger of the two.
+    E_end, H_end = r.main.fields()
+    field_scale = 2.0 * np.sqrt(np.sum(np.abs(np.concatenate([E_end, H_end], 1)) ** 2)
+                                * got.size / (E_end.size + H_end.size))
+    err_x = np.linalg.norm(got - exp) / max(np.linalg.norm(exp), field_scale)
+    assert err_x <= TOL, (err_x, rel_l2(got, exp))
+    assert s.incident_amplitude() == pytest.approx(r.incident_amplitude(), rel=TOL)
+
+
+def _far_field_oracle(r, p):
+    from oracle import ntff
+    k = 2 * math.pi / p.wave.wavelength
+    th, ph = angles(p.mode)
+    return ntff.far_field(r.phasors(), p.wave.ntff_lo, p.wave.ntff_hi, k, p.wave.center,
+                          r.incident_amplitude(), p.mode, th, ph)
+
+
+@pytest.mark.parametrize("mode", ["ez", "hz"])
+def test_cylinder_parity_fp32(mode):
+    """The 1024^2 cylinder workload at reduced size: n = 160, lambda = 16, x = 5."""
+    p = W.cylinder_problem(n=160, x=5.0, wavelength=16.0, eps_in=2.25, w=12, mode=mode, periods=20)
+    s = gpu_solver(p)
+    r = oracle_run(p)
+    assert rel_l2(s.populations(), oracle_to_planes(r.main.f, mode, p.shape)) <= TOL
+    th, ph = angles(mode)
+    s2 = s.far_field(th, ph)
+    s2_ref = _far_field_oracle(r, p)
+    assert rel_l2(s2, s2_ref) <= TOL
+
+
+def test_sphere_subproblem_parity_fp32():
+    """The 64^3 parity subproblem of the 384^3 sphere (W = 8, lambda = 16, x = 5, 480 steps)."""
+    p = W.sphere_subproblem()
+    s = gpu_solver(p)
+    r = oracle_run(p)
+    assert rel_l2(s.populations(), oracle_to_planes(r.main.f, "3d", p.shape)) <= TOL
+    th, ph = angles("3d")
+    assert rel_l2(s.far_field(th, ph), _far_field_oracle(r, p)) <= TOL
+
+
+@pytest.mark.parametrize("storage,bound", [("f16", 2e-2), ("bf16", 1.5e-1)])
+def test_reduced_storage_error_is_bounded(storage, bound, capsys):
+    p = W.cylinder_problem(n=160, x=5.0, wavelength=16.0, eps_in=2.25, w=12, mode="ez", periods=20)
+    s = gpu_solver(p, storage=storage)
+    r = oracle_run(p)
+    err = rel_l2(s.populations(), oracle_to_planes(r.main.f, "ez", p.shape))
+    th, _ = angles("ez")
+    s2 = s.far_field(th)
+    s2_ref = _far_field_oracle(r, p)
+    from oracle import metrics
+    rms = metrics.normalized_rms(s2, s2_ref)
+    with capsys.disabled():
+        print(f"\n[{storage}] population rel-L2 vs FP64 oracle {err:.3e}; |S|^2 normalized RMS {rms:.3e}")
+    assert err < bound
+    assert rms < bound
+
+
+@pytest.mark.parametrize("mode,shape", [("ez", (5, 7, 1)), ("hz", (33, 3, 1)), ("ez", (129, 2, 1)),
+                                        ("3d", (3, 3, 2)), ("3d", (33, 5, 4)), ("3d", (1, 1, 9))])
+def test_edge_shapes_without_source(mode, shape):
+    """Tiny and ragged grids (no source, absorbing layer where it fits)."""
+    eps = W.random_eps(shape, 1.0, 6.0, 7)
+    minext = min(s for s in shape[:2 if mode != "3d" else 3])
+    w = 1 if minext >= 4 else 0
+    p = W.Problem("edge", mode, shape, eps, w, 0.3, None, 9, 1)
+    init = W.random_state(mode, shape, 11)
+    s = gpu_solver(p, init=init, steps=0)
+    s.step(9)
+    from oracle import lb
+    lat = lb.Lattice(shape, eps, sponge_w=w, sigma_max=0.3)
+    lat.f = planes_to_oracle(init.astype(np.float64), mode)
+    for n in range(9):
+        lat.step(n)
+    assert rel_l2(s.populations(), oracle_to_planes(lat.f, mode, shape)) <= TOL
+
+
+def test_checkpoint_round_trip_and_energy():
+    p = W.cylinder_problem(n=96, x=3.0, wavelength=12.0, eps_in=3.0, w=8, mode="ez", periods=6)
+    from paper_2510_11042_gb300 import lbem
+    a = gpu_solver(p, steps=100)
+    snap = lbem.lbem_save_state(a.h)
+    a.step(50)
+    ref = a.populations()
+    b = gpu_solver(p, steps=0)
+    lbem.lbem_load_state(b.h, snap)
+    assert b.time == 100
+    b.step(50)
+    np.testing.assert_array_equal(b.populations(), ref)
+    # energy matches the oracle's energy of the same state
+    r = oracle_run(p, steps=150)
+    assert a.energy() == pytest.approx(r.main.energy(), rel=1e-5)
+
+
+def test_nonfinite_state_is_reported():
+    from paper_2510_11042_gb300 import lbem
+    p = W.cylinder_problem(n=64, x=2.0, wavelength=8.0, eps_in=2.0, w=6, mode="ez", periods=2)
+    s = gpu_solver(p, steps=5)
+    pops = s.populations()
+    pops[3, 0, 10, 10] = np.nan
+    s.set_populations(pops)
+    with pytest.raises(lbem.LbemError) as ei:
+        s.energy()
+    assert ei.value.code == lbem.LBEM_ERR_NONFINITE
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2510_11042_gb300 import lbem
+    p = W.cylinder_problem(n=64, x=2.0, wavelength=8.0, eps_in=2.0, w=6, mode="ez", periods=2)
+    s = gpu_solver(p, steps=0, dft=False)
+    bad = W.axis_wave("ez", p.shape, 6, 8.0)
+    bad.polarization = (0.0, 1.0, 0.0)          # EZ needs E along z
+    with pytest.raises(lbem.LbemError) as ei:
+        s.inject(bad)
+    assert ei.value.code == lbem.LBEM_ERR_ARG
+    bad = W.axis_wave("ez", p.shape, 6, 8.1)     # 3*lambda not an integer
+    with pytest.raises(lbem.LbemError):
+        s.inject(bad)
+    bad = W.axis_wave("ez", p.shape, 6, 8.0)
+    bad.tf_lo = (2, 2, 0)                        # TF box inside the absorbing layer
+    with pytest.raises(lbem.LbemError):
+        s.inject(bad)
+    eps = np.full((1, 64, 64), 0.5, np.float32)  # eps_r < 1 is not a dielectric
+    with pytest.raises(lbem.LbemError):
+        lbem.lbem_set_permittivity(s.h, eps)

@@ -97,11 +97,16 @@ def cylinder_eps(n: int, a: float, eps_in: float) -> np.ndarray:
     return eps[None, :, :]
 
 
-def sphere_eps(n: int, a: float, eps_in: float) -> np.ndarray:
+def sphere_eps(n: int, a: float, eps_in: float, z_range=None) -> np.ndarray:
+    """[nz][ny][nx] map of the n^3 cube; z_range = (z0, z1) gives only that slab."""
     c = centre(n)
-    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-    inside = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2 <= a * a
-    return np.where(inside, eps_in, 1.0).astype(np.float32)
+    z0, z1 = z_range if z_range is not None else (0, n)
+    out = np.ones((z1 - z0, n, n), np.float32)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    r2 = (x - c) ** 2 + (y - c) ** 2
+    for k, z in enumerate(range(z0, z1)):
+        out[k][r2 + (z - c) ** 2 <= a * a] = eps_in
+    return out
 
 
 def hexagon_eps(n: int, side: float, eps_in: float) -> np.ndarray:
