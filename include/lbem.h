@@ -68,8 +68,11 @@ typedef struct lbem_ctx *lbem_handle;
 typedef enum { LBEM_D3Q7 = 0 } lbem_velocity_set;
 
 /* Storage type of the populations in device memory.  The update arithmetic is
- * float32 in every case; F16/BF16 store each population plane scaled by a
- * power of two (see lbem_set_storage_scales) and round to nearest even. */
+ * float32 in every case; F16/BF16 store populations divided by one power-of-two
+ * scale (see lbem_set_storage_scale) and round to nearest even.  Inside the
+ * total-field box the stored values are the scattered part (the total minus
+ * the incident line's populations), elsewhere the scattered field itself, so
+ * the storage rounding error is relative to the scattered field. */
 typedef enum { LBEM_F32 = 0, LBEM_F16 = 1, LBEM_BF16 = 2 } lbem_storage;
 
 typedef enum { LBEM_MODE_EZ = 0, LBEM_MODE_HZ = 1, LBEM_MODE_3D = 2 } lbem_mode;
@@ -200,11 +203,12 @@ int32_t lbem_state_bytes(lbem_handle h, size_t *bytes_out);
 int32_t lbem_save_state(lbem_handle h, void *buf_host, size_t bytes);
 int32_t lbem_load_state(lbem_handle h, const void *buf_host, size_t bytes);
 
-/* Power-of-two scales of the reduced-precision storage, one per plane q:
- * stored = population / scale.  Ignored for LBEM_F32.  Values must be exact
- * powers of two. */
-int32_t lbem_set_storage_scales(lbem_handle h, const float *scales_host);
-int32_t lbem_get_storage_scales(lbem_handle h, float *scales_host);
+/* Power-of-two scale of the reduced-precision storage, shared by all planes:
+ * stored = population / scale (default 2^-10 for F16, 1 for BF16; always 1 for
+ * LBEM_F32, where the call is a no-op).  Setting it rescales the stored state.
+ * One scale for all planes lets the linear update run in storage units. */
+int32_t lbem_set_storage_scale(lbem_handle h, float scale);
+int32_t lbem_get_storage_scale(lbem_handle h, float *scale_out);
 
 /* Wait for the handle's stream; reports an asynchronous CUDA error. */
 int32_t lbem_sync(lbem_handle h);

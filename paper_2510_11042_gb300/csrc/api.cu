@@ -12,7 +12,7 @@
 #include "lbem_internal.cuh"
 
 namespace lbem {
-int step_block_x();
+int step_cells_per_block();
 }
 
 using namespace lbem;
@@ -33,7 +33,7 @@ struct lbem_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     float *inv_eps = nullptr;
-    float *line[2] = {nullptr, nullptr};
+    float *line[3] = {nullptr, nullptr, nullptr};  // incident line at t, t+1, t+2 (mod 3)
     int n_line_max = 0;
     double *dft = nullptr;
     size_t dft_doubles_max = 0;
@@ -53,7 +53,7 @@ struct lbem_ctx {
     size_t dft_doubles = 0;
     int64_t dft_t0 = -1;
     int dft_periods = 0;
-    float scale[kMaxQ], inv_scale[kMaxQ];
+    float scale = 1.f, inv_scale = 1.f;  // stored population = population / scale
     int64_t launches = 0;
     char err[512];
 };
@@ -84,7 +84,7 @@ static int cuda_fail(lbem_ctx *h, cudaError_t e, const char *what)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t f0, f1, inv_eps, line0, line1, dft, line_dft, scratch, stage, flag, total;
+    size_t f0, f1, inv_eps, line0, line1, line2, dft, line_dft, scratch, stage, flag, total;
     int Q, nxp, n_line_max;
     long long P, ncell;
     size_t elem, dft_doubles_max, scratch_doubles;
@@ -134,6 +134,7 @@ static Layout make_layout(const lbem_grid_desc *g)
     L.inv_eps = take((size_t)L.P * 4);
     L.line0 = take((size_t)L.Q * L.n_line_max * 4);
     L.line1 = take((size_t)L.Q * L.n_line_max * 4);
+    L.line2 = take((size_t)L.Q * L.n_line_max * 4);
     L.dft = take(L.dft_doubles_max * 8);
     L.line_dft = take((size_t)L.n_line_max * 6 * 8);
     L.scratch = take(L.scratch_doubles * 8);
@@ -143,24 +144,88 @@ static Layout make_layout(const lbem_grid_desc *g)
     return L;
 }
 
-static void default_scales(lbem_ctx *h, double amplitude, double eps_max)
+// One power-of-two scale for all planes of reduced-precision storage.  The
+// stored values are scattered fields; 2^-10 keeps populations up to +-64 below
+// the FP16 maximum (65504) and leaves values down to ~6e-8 normal.  BF16 has
+// the FP32 exponent range and needs no scaling.
+static void default_scale(lbem_ctx *h)
 {
-    // populations of a unit-amplitude field stay within a few units; keep them
-    // near 2^12 in the stored format.  The rest population e_0 ~ (eps-1) E.
-    for (int q = 0; q < kMaxQ; ++q) {
-        h->scale[q] = 1.f;
-        h->inv_scale[q] = 1.f;
+    h->scale = h->g.storage == LBEM_F16 ? std::ldexp(1.0f, -10) : 1.0f;
+    h->inv_scale = 1.0f / h->scale;
+}
+
+static double ramp(double t, double tr)
+{
+    if (t <= 0) return 0.0;
+    if (t >= tr) return 1.0;
+    return 0.5 * (1.0 - std::cos(M_PI * t / tr));
+}
+
+// Hard-source fields of the incident line at time t: E = E0 ramp(t) sin(w t) p, H = k x E.
+static void source_fields(const lbem_ctx *h, int64_t t, float E[3], float H[3])
+{
+    const double *d = h->wave.dir, *p = h->wave.pol;
+    const double kxp[3] = {d[1] * p[2] - d[2] * p[1], d[2] * p[0] - d[0] * p[2],
+                           d[0] * p[1] - d[1] * p[0]};
+    const double ph = 2.0 * M_PI * (double)(t % h->T) / (double)h->T;
+    const double s = h->wave.amplitude * ramp((double)t, h->wave.ramp_periods * h->T) * std::sin(ph);
+    for (int c = 0; c < 3; ++c) {
+        E[c] = (float)(s * p[c]);
+        H[c] = (float)(s * kxp[c]);
     }
-    if (h->g.storage == LBEM_F32) return;
-    const double a = amplitude > 0 ? amplitude : 1.0;
-    for (int q = 0; q < h->Q; ++q) {
-        const bool rest_e = (q < (h->g.mode == 0 ? 1 : (h->g.mode == 1 ? 2 : 3)));
-        double span = 4.0 * a * (rest_e ? std::max(1.0, eps_max) : 1.0);
-        int e2 = (int)std::ceil(std::log2(span));
-        const float s = std::ldexp(1.0f, e2 - 14);
-        h->scale[q] = s;
-        h->inv_scale[q] = 1.0f / s;
+}
+
+static float *line_at(lbem_ctx *h, int64_t t) { return h->line[(int)(((t % 3) + 3) % 3)]; }
+
+static IncView inc_view(lbem_ctx *h)
+{
+    IncView v;
+    std::memset(&v, 0, sizeof v);
+    if (!h->has_wave) return v;
+    v.on = 1;
+    for (int k = 0; k < 3; ++k) {
+        v.tf_lo[k] = h->wave.tfsf_lo[k];
+        v.tf_hi[k] = h->wave.tfsf_hi[k];
     }
+    v.axis = h->inc_axis;
+    v.line = line_at(h, h->t);
+    v.n = h->n_line;
+    return v;
+}
+
+static void fill_common_args(lbem_ctx *h, StepArgs &a)
+{
+    std::memset(&a, 0, sizeof a);
+    const int BX = step_cells_per_block();
+    a.inv_eps = h->inv_eps;
+    a.nx = h->g.nx; a.ny = h->g.ny; a.nz = h->g.nz; a.nxp = h->nxp;
+    a.P = h->P;
+    a.nblk_x = (h->g.nx + BX - 1) / BX;
+    a.nblk_main = a.nblk_x * h->g.ny * h->g.nz;
+    a.w = h->g.absorber_width;
+    a.sigma_max = (float)h->g.sigma_max;
+    a.inv_w = a.w > 0 ? 1.0f / (float)a.w : 0.f;
+    a.scale = h->scale;
+    a.inv_scale = h->inv_scale;
+    if (!h->has_wave) return;
+    a.tfsf = 1;
+    a.line_on = 1;
+    for (int k = 0; k < 3; ++k) {
+        a.tf_lo[k] = h->wave.tfsf_lo[k];
+        a.tf_hi[k] = h->wave.tfsf_hi[k];
+        a.nt_lo[k] = h->wave.ntff_lo[k];
+        a.nt_hi[k] = h->wave.ntff_hi[k];
+    }
+    a.inc_axis = h->inc_axis;
+    a.n_line = h->n_line;
+    a.src_index = h->src_index;
+    a.dft = h->dft;
+    for (int f = 0; f < h->faces.nfaces; ++f) {
+        a.face_off[f] = h->faces.off[f];
+        a.face_nu[f] = h->faces.nu[f];
+        a.face_nv[f] = h->faces.nv[f];
+    }
+    a.line_dft = h->line_dft;
 }
 
 extern "C" {
@@ -242,6 +307,7 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->inv_eps = (float *)(h->ws + L.inv_eps);
     h->line[0] = (float *)(h->ws + L.line0);
     h->line[1] = (float *)(h->ws + L.line1);
+    h->line[2] = (float *)(h->ws + L.line2);
     h->n_line_max = L.n_line_max;
     h->dft = (double *)(h->ws + L.dft);
     h->dft_doubles_max = L.dft_doubles_max;
@@ -250,7 +316,7 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->scratch_doubles = L.scratch_doubles;
     h->stage = (float *)(h->ws + L.stage);
     h->flag = (int *)(h->ws + L.flag);
-    default_scales(h, 1.0, 1.0);
+    default_scale(h);
     int rc = LBEM_OK;
     cudaError_t e = cudaMemsetAsync(h->f[0], 0, (size_t)L.Q * L.P * L.elem, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, (size_t)L.Q * L.P * L.elem, h->stream);
@@ -356,6 +422,13 @@ int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
     int src = w->source_index < 0 ? W + 2 : w->source_index;
     if (src < 0 || src >= w->tfsf_lo[ax] - 1)
         return fail(h, LBEM_ERR_ARG, "source_index must lie upstream of the total-field box");
+    if (h->has_wave) {
+        // the stored state holds scattered parts inside the old box: make it total again
+        CK(h, launch_add_incident(h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx, h->g.ny,
+                                  h->g.nz, h->nxp, inc_view(h), 1.0f, h->stream));
+        h->launches += 1;
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     h->wave = *w;
     h->wave.source_index = src;
     h->has_wave = true;
@@ -367,10 +440,18 @@ int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
     build_faces(h);
     h->dft_t0 = -1;
     h->dft_periods = 0;
-    CK(h, cudaMemsetAsync(h->line[0], 0, (size_t)h->Q * h->n_line_max * 4, h->stream));
-    CK(h, cudaMemsetAsync(h->line[1], 0, (size_t)h->Q * h->n_line_max * 4, h->stream));
+    for (int k = 0; k < 3; ++k)
+        CK(h, cudaMemsetAsync(h->line[k], 0, (size_t)h->Q * h->n_line_max * 4, h->stream));
     CK(h, cudaMemsetAsync(h->line_dft, 0, (size_t)h->n_line_max * 6 * 8, h->stream));
     CK(h, cudaMemsetAsync(h->dft, 0, h->dft_doubles * 8, h->stream));
+    // the line runs one step ahead: line(t) = 0, line(t+1) = one update of it
+    StepArgs a;
+    fill_common_args(h, a);
+    a.line_n = line_at(h, h->t);
+    a.line_out = line_at(h, h->t + 1);
+    source_fields(h, h->t + 1, a.src_E, a.src_H);
+    CK(h, launch_line_init(h->g.mode, a, h->stream));
+    h->launches += 1;
     return LBEM_OK;
 }
 
@@ -386,78 +467,31 @@ int32_t lbem_set_dft_window(lbem_handle h, int64_t t_start, int32_t n_periods)
     return LBEM_OK;
 }
 
-static double ramp(double t, double tr)
-{
-    if (t <= 0) return 0.0;
-    if (t >= tr) return 1.0;
-    return 0.5 * (1.0 - std::cos(M_PI * t / tr));
-}
-
 int32_t lbem_step(lbem_handle h, int64_t n)
 {
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
     if (n < 0) return fail(h, LBEM_ERR_ARG, "n must be >= 0");
     StepArgs a;
-    std::memset(&a, 0, sizeof a);
-    const int BX = step_block_x();
-    a.inv_eps = h->inv_eps;
-    a.nx = h->g.nx; a.ny = h->g.ny; a.nz = h->g.nz; a.nxp = h->nxp;
-    a.P = h->P;
-    a.nblk_x = (h->g.nx + BX - 1) / BX;
-    a.nblk_main = a.nblk_x * h->g.ny * h->g.nz;
-    a.w = h->g.absorber_width;
-    a.sigma_max = (float)h->g.sigma_max;
-    a.inv_w = a.w > 0 ? 1.0f / (float)a.w : 0.f;
-    for (int q = 0; q < kMaxQ; ++q) {
-        a.scale[q] = h->scale[q];
-        a.inv_scale[q] = h->inv_scale[q];
-    }
-    if (h->has_wave) {
-        a.tfsf = 1;
-        a.line_on = 1;
-        for (int k = 0; k < 3; ++k) {
-            a.tf_lo[k] = h->wave.tfsf_lo[k];
-            a.tf_hi[k] = h->wave.tfsf_hi[k];
-            a.nt_lo[k] = h->wave.ntff_lo[k];
-            a.nt_hi[k] = h->wave.ntff_hi[k];
-        }
-        a.inc_axis = h->inc_axis;
-        a.n_line = h->n_line;
-        a.src_index = h->src_index;
-        a.dft = h->dft;
-        for (int f = 0; f < h->faces.nfaces; ++f) {
-            a.face_off[f] = h->faces.off[f];
-            a.face_nu[f] = h->faces.nu[f];
-            a.face_nv[f] = h->faces.nv[f];
-        }
-        a.line_dft = h->line_dft;
-    }
-    double kxp[3] = {0, 0, 0};
-    if (h->has_wave) {
-        const double *d = h->wave.dir, *p = h->wave.pol;
-        kxp[0] = d[1] * p[2] - d[2] * p[1];
-        kxp[1] = d[2] * p[0] - d[0] * p[2];
-        kxp[2] = d[0] * p[1] - d[1] * p[0];
-    }
+    fill_common_args(h, a);
     for (int64_t k = 0; k < n; ++k) {
         const int64_t t = h->t + 1;  // time of the fields this step computes
-        a.fin = h->f[h->cur];
-        a.fout = h->f[h->cur ^ 1];
+        const size_t plane_bytes = (size_t)h->P * h->elem;
+        for (int q = 0; q < h->Q; ++q) {
+            a.fin_q[q] = (const char *)h->f[h->cur] + q * plane_bytes;
+            a.fout_q[q] = (char *)h->f[h->cur ^ 1] + q * plane_bytes;
+        }
         if (h->has_wave) {
-            a.inc = h->line[h->cur];
-            a.line_in = h->line[h->cur];
-            a.line_out = h->line[h->cur ^ 1];
-            const double ph = 2.0 * M_PI * (double)(t % h->T) / (double)h->T;
-            const double s = h->wave.amplitude * ramp((double)t, h->wave.ramp_periods * h->T) * std::sin(ph);
-            for (int c = 0; c < 3; ++c) {
-                a.src_E[c] = (float)(s * h->wave.pol[c]);
-                a.src_H[c] = (float)(s * kxp[c]);
-            }
+            a.line_n = line_at(h, h->t);
+            a.line_n1 = line_at(h, h->t + 1);
+            a.line_out = line_at(h, h->t + 2);
+            source_fields(h, h->t + 2, a.src_E, a.src_H);
             a.dft_on = (h->dft_t0 >= 1 && t >= h->dft_t0 && t < h->dft_t0 + (int64_t)h->dft_periods * h->T);
             if (a.dft_on) {
+                const double ph = 2.0 * M_PI * (double)(t % h->T) / (double)h->T;
                 a.dft_c = std::cos(ph);
                 a.dft_s = std::sin(ph);
-                a.dft_scale = 2.0 / ((double)h->dft_periods * h->T);
+                a.dft_scale = 2.0 / ((double)h->dft_periods * h->T);  // line (FP32, unscaled)
+                a.dft_scale_cells = a.dft_scale * h->scale;            // lattice (storage units)
             }
         }
         cudaError_t e = launch_step(h->g.mode, h->g.storage, a, h->stream);
@@ -564,8 +598,8 @@ int32_t lbem_get_populations(lbem_handle h, float *out, int32_t on_device)
     if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
     for (int q = 0; q < h->Q; ++q) {
         float *dst = on_device ? out + (size_t)q * h->ncell : h->stage;
-        CK(h, launch_pack(h->g.storage, h->f[h->cur], h->P, q, h->scale[q], dst, h->g.nx, h->g.ny,
-                          h->g.nz, h->nxp, h->stream));
+        CK(h, launch_pack(h->g.storage, h->f[h->cur], h->P, q, h->scale, dst, h->g.nx, h->g.ny,
+                          h->g.nz, h->nxp, inc_view(h), h->stream));
         h->launches += 1;
         if (!on_device)
             CK(h, cudaMemcpyAsync(out + (size_t)q * h->ncell, h->stage, (size_t)h->ncell * 4,
@@ -584,8 +618,8 @@ int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t on_device)
             CK(h, cudaMemcpyAsync(h->stage, src, (size_t)h->ncell * 4, cudaMemcpyHostToDevice, h->stream));
             src = h->stage;
         }
-        CK(h, launch_unpack(h->g.storage, h->f[h->cur], h->P, q, h->inv_scale[q], src, h->g.nx,
-                            h->g.ny, h->g.nz, h->nxp, h->stream));
+        CK(h, launch_unpack(h->g.storage, h->f[h->cur], h->P, q, h->inv_scale, src, h->g.nx,
+                            h->g.ny, h->g.nz, h->nxp, inc_view(h), h->stream));
         h->launches += 1;
         if (!on_device) CK(h, cudaStreamSynchronize(h->stream));  // stage is reused
     }
@@ -599,7 +633,7 @@ int32_t lbem_fields(lbem_handle h, float *E, float *H, int32_t on_device)
         float *dst = (comp < 3 ? E : H) + (size_t)(comp % 3) * h->ncell;
         float *out = on_device ? dst : h->stage;
         CK(h, launch_fields(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->scale, h->P,
-                            h->g.nx, h->g.ny, h->g.nz, h->nxp, comp, out, h->stream));
+                            h->g.nx, h->g.ny, h->g.nz, h->nxp, inc_view(h), comp, out, h->stream));
         h->launches += 1;
         if (!on_device) {
             CK(h, cudaMemcpyAsync(dst, h->stage, (size_t)h->ncell * 4, cudaMemcpyDeviceToHost, h->stream));
@@ -634,8 +668,8 @@ int32_t lbem_energy(lbem_handle h, double *out)
     double *part = h->scratch + 8;
     int l = 0;
     CK(h, launch_energy(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->scale, h->P, h->g.nx,
-                        h->g.ny, h->g.nz, h->nxp, part, (int)(h->scratch_doubles - 8), d_out,
-                        h->stream, &l));
+                        h->g.ny, h->g.nz, h->nxp, inc_view(h), part, (int)(h->scratch_doubles - 8),
+                        d_out, h->stream, &l));
     h->launches += l;
     CK(h, cudaMemcpyAsync(out, d_out, 8, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -654,7 +688,7 @@ struct StateHeader {
 int32_t lbem_state_bytes(lbem_handle h, size_t *bytes)
 {
     if (!h || !bytes) return fail(h, LBEM_ERR_ARG, "NULL argument");
-    *bytes = sizeof(StateHeader) + (size_t)h->Q * h->P * h->elem + (size_t)h->Q * h->n_line_max * 4 +
+    *bytes = sizeof(StateHeader) + (size_t)h->Q * h->P * h->elem + 2 * (size_t)h->Q * h->n_line_max * 4 +
              (size_t)h->n_line_max * 48 + h->dft_doubles_max * 8;
     return LBEM_OK;
 }
@@ -680,8 +714,10 @@ int32_t lbem_save_state(lbem_handle h, void *buf, size_t bytes)
     p += sizeof hd;
     CK(h, cudaMemcpyAsync(p, h->f[h->cur], hd.pop_bytes, cudaMemcpyDeviceToHost, h->stream));
     p += hd.pop_bytes;
-    CK(h, cudaMemcpyAsync(p, h->line[h->cur], hd.line_bytes, cudaMemcpyDeviceToHost, h->stream));
-    p += hd.line_bytes;
+    for (int k = 0; k < 2; ++k) {  // incident line at t and t+1
+        CK(h, cudaMemcpyAsync(p, line_at(h, h->t + k), hd.line_bytes, cudaMemcpyDeviceToHost, h->stream));
+        p += hd.line_bytes;
+    }
     CK(h, cudaMemcpyAsync(p, h->line_dft, hd.line_dft_bytes, cudaMemcpyDeviceToHost, h->stream));
     p += hd.line_dft_bytes;
     CK(h, cudaMemcpyAsync(p, h->dft, hd.dft_bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -703,8 +739,11 @@ int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
     const char *p = (const char *)buf + sizeof hd;
     CK(h, cudaMemcpyAsync(h->f[h->cur], p, hd.pop_bytes, cudaMemcpyHostToDevice, h->stream));
     p += hd.pop_bytes;
-    CK(h, cudaMemcpyAsync(h->line[h->cur], p, hd.line_bytes, cudaMemcpyHostToDevice, h->stream));
-    p += hd.line_bytes;
+    for (int k = 0; k < 2; ++k) {  // incident line at t and t+1 of the snapshot
+        CK(h, cudaMemcpyAsync(h->line[(int)((hd.t + k) % 3)], p, hd.line_bytes, cudaMemcpyHostToDevice,
+                              h->stream));
+        p += hd.line_bytes;
+    }
     CK(h, cudaMemcpyAsync(h->line_dft, p, hd.line_dft_bytes, cudaMemcpyHostToDevice, h->stream));
     p += hd.line_dft_bytes;
     CK(h, cudaMemcpyAsync(h->dft, p, hd.dft_bytes, cudaMemcpyHostToDevice, h->stream));
@@ -713,26 +752,35 @@ int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
     return LBEM_OK;
 }
 
-int32_t lbem_set_storage_scales(lbem_handle h, const float *scales)
+int32_t lbem_set_storage_scale(lbem_handle h, float scale)
 {
-    if (!h || !scales) return fail(h, LBEM_ERR_ARG, "NULL argument");
-    for (int q = 0; q < h->Q; ++q) {
-        int e;
-        const float m = std::frexp(scales[q], &e);
-        if (!(scales[q] > 0) || m != 0.5f) return fail(h, LBEM_ERR_ARG, "scale %d is not a power of two", q);
-    }
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    int e;
+    if (!(scale > 0) || !std::isfinite(scale) || std::frexp(scale, &e) != 0.5f)
+        return fail(h, LBEM_ERR_ARG, "scale must be a positive power of two");
     if (h->g.storage == LBEM_F32) return LBEM_OK;
-    for (int q = 0; q < h->Q; ++q) {
-        h->scale[q] = scales[q];
-        h->inv_scale[q] = 1.0f / scales[q];
+    // rescale the stored state so that it keeps its value
+    const float ratio = h->scale / scale;
+    if (ratio != 1.0f) {
+        IncView none;
+        std::memset(&none, 0, sizeof none);
+        for (int q = 0; q < h->Q; ++q) {
+            CK(h, launch_pack(h->g.storage, h->f[h->cur], h->P, q, ratio, h->stage, h->g.nx, h->g.ny,
+                              h->g.nz, h->nxp, none, h->stream));
+            CK(h, launch_unpack(h->g.storage, h->f[h->cur], h->P, q, 1.0f, h->stage, h->g.nx, h->g.ny,
+                                h->g.nz, h->nxp, none, h->stream));
+            h->launches += 2;
+        }
     }
+    h->scale = scale;
+    h->inv_scale = 1.0f / scale;
     return LBEM_OK;
 }
 
-int32_t lbem_get_storage_scales(lbem_handle h, float *scales)
+int32_t lbem_get_storage_scale(lbem_handle h, float *scale)
 {
-    if (!h || !scales) return fail(h, LBEM_ERR_ARG, "NULL argument");
-    for (int q = 0; q < h->Q; ++q) scales[q] = h->scale[q];
+    if (!h || !scale) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    *scale = h->scale;
     return LBEM_OK;
 }
 

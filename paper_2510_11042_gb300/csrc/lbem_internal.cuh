@@ -53,8 +53,8 @@ inline int dft_comps_of_mode(int mode) { return mode == 2 ? 6 : 3; }
 
 // Arguments of the fused step kernel (passed by value).
 struct StepArgs {
-    const void *fin;
-    void *fout;
+    const void *fin_q[kMaxQ];  // start of each input population plane
+    void *fout_q[kMaxQ];       // start of each output population plane
     const float *inv_eps;
     int nx, ny, nz, nxp;       // extent and padded row pitch (elements)
     long long P;               // plane stride in elements = nz*ny*nxp
@@ -63,32 +63,46 @@ struct StepArgs {
     // absorbing layer
     int w;
     float sigma_max, inv_w;
-    // TF/SF source
+    // TF/SF source: the incident line at time n+1 ([Q][n_line]); line_n is
+    // used only to start a fresh line
     int tfsf;
     int tf_lo[3], tf_hi[3];
     int inc_axis;
-    const float *inc;          // incident line at time n: [Q][n_line]
+    const float *line_n;
+    const float *line_n1;
     int n_line;
     // DFT of the near fields on the NTFF box surface
     int dft_on;
-    double dft_c, dft_s, dft_scale;
+    double dft_c, dft_s;
+    double dft_scale;          // 2/(P T): incident line (FP32 units)
+    double dft_scale_cells;    // 2/(P T) times the storage scale: lattice cells
     int nt_lo[3], nt_hi[3];
     double *dft;
     long long face_off[kMaxFaces];
     int face_nu[kMaxFaces], face_nv[kMaxFaces];
-    // incident line update (executed by one extra block)
+    // incident line update line(n+1) -> line(n+2) (first blocks of the launch)
     int line_on;
-    const float *line_in;
     float *line_out;
     int src_index;
-    float src_E[3], src_H[3];
+    float src_E[3], src_H[3];  // hard-source fields at time n+2
     double *line_dft;          // [n_line][3][2]
-    // reduced-precision storage scales
-    float scale[kMaxQ], inv_scale[kMaxQ];
+    // reduced-precision storage: stored = population / scale (power of two)
+    float scale, inv_scale;
 };
 
 // Launchers (step.cu)
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
+cudaError_t launch_line_init(int mode, const StepArgs &a, cudaStream_t s);
+
+// Where the stored populations hold the scattered part G = F - I (inside the
+// total-field box), diagnostics add the incident line back.
+struct IncView {
+    int on;
+    int tf_lo[3], tf_hi[3];
+    int axis;
+    const float *line;         // incident line at the state's time, [Q][n]
+    int n;
+};
 
 // Observables and data movement (observe.cu)
 struct FaceGeom {
@@ -121,15 +135,19 @@ cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launche
 cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int nz, int nxp,
                            int *bad_flag, cudaStream_t s);
 cudaError_t launch_pack(int storage, const void *f, long long P, int q, float scale, float *out,
-                        int nx, int ny, int nz, int nxp, cudaStream_t s);
+                        int nx, int ny, int nz, int nxp, const IncView &inc, cudaStream_t s);
 cudaError_t launch_unpack(int storage, void *f, long long P, int q, float inv_scale,
-                          const float *in, int nx, int ny, int nz, int nxp, cudaStream_t s);
+                          const float *in, int nx, int ny, int nz, int nxp, const IncView &inc,
+                          cudaStream_t s);
+cudaError_t launch_add_incident(int storage, void *f, long long P, int Q, float scale,
+                                int nx, int ny, int nz, int nxp, const IncView &inc, float sign,
+                                cudaStream_t s);
 cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps,
-                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
-                          int comp, float *out, cudaStream_t s);
+                          float scale, long long P, int nx, int ny, int nz, int nxp,
+                          const IncView &inc, int comp, float *out, cudaStream_t s);
 cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps,
-                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
-                          double *partial, int max_partial, double *out, cudaStream_t s,
-                          int *launches);
+                          float scale, long long P, int nx, int ny, int nz, int nxp,
+                          const IncView &inc, double *partial, int max_partial, double *out,
+                          cudaStream_t s, int *launches);
 
 }  // namespace lbem

@@ -208,41 +208,77 @@ __global__ void inv_eps_kernel(const float *eps, float *inv_eps, int nx, int ny,
 }
 
 // ------------------------------------------------------------ pack / unpack
+// Incident population of plane q at cell (x, y, z) when it lies in the
+// total-field box (where the stored value is the scattered part), else 0.
+__device__ __forceinline__ float inc_at(const IncView &v, int q, int x, int y, int z)
+{
+    if (!v.on) return 0.f;
+    if (x < v.tf_lo[0] || x > v.tf_hi[0] || y < v.tf_lo[1] || y > v.tf_hi[1] || z < v.tf_lo[2] ||
+        z > v.tf_hi[2])
+        return 0.f;
+    const int s = v.axis == 0 ? x : (v.axis == 1 ? y : z);
+    return v.line[(size_t)q * v.n + s];
+}
+
 template <class S>
-__global__ void pack_kernel(const S *f, float scale, float *out, int nx, long long ncell, int nxp)
+__global__ void pack_kernel(const S *f, int q, float scale, float *out, int nx, int ny,
+                            long long ncell, int nxp, IncView inc)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % nx);
         const long long r = i / nx;
-        out[i] = ldv<S>(f + r * nxp + x) * scale;
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        out[i] = ldv<S>(f + r * nxp + x) * scale + inc_at(inc, q, x, y, z);
     }
 }
 
 template <class S>
-__global__ void unpack_kernel(S *f, float inv_scale, const float *in, int nx, long long ncell, int nxp)
+__global__ void unpack_kernel(S *f, int q, float inv_scale, const float *in, int nx, int ny,
+                              long long ncell, int nxp, IncView inc)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % nx);
         const long long r = i / nx;
-        stv<S>(f + r * nxp + x, in[i] * inv_scale);
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        stv<S>(f + r * nxp + x, (in[i] - inc_at(inc, q, x, y, z)) * inv_scale);
+    }
+}
+
+// Convert the stored populations of the total-field box between the scattered
+// part and the total (sign = +1: add the incident line, -1: remove it).
+template <class S>
+__global__ void add_incident_kernel(S *f, long long P, int Q, float scale, int nx, int ny,
+                                    long long ncell, int nxp, IncView inc, float sign)
+{
+    const float inv = 1.0f / scale;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long r = i / nx;
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        for (int q = 0; q < Q; ++q) {
+            const float add = inc_at(inc, q, x, y, z);
+            if (add == 0.f) continue;
+            S *p = f + q * P + r * nxp + x;
+            stv<S>(p, (ldv<S>(p) * scale + sign * add) * inv);
+        }
     }
 }
 
 // ------------------------------------------------------------ fields & energy
-struct ScaleTab { float s[kMaxQ]; };
-
 template <int MODE, class S>
-__device__ __forceinline__ void cell_DB(const S *f, const ScaleTab &sc, long long P, long long c,
-                                        float D[3], float B[3])
+__device__ __forceinline__ void cell_DB(const S *f, float sc, long long P, long long c,
+                                        const IncView &inc, int x, int y, int z, float D[3],
+                                        float B[3])
 {
     using PL = Planes<MODE>;
     D[0] = D[1] = D[2] = 0.f;
     B[0] = B[1] = B[2] = 0.f;
 #pragma unroll
     for (int q = 0; q < PL::Q; ++q) {
-        const float v = ldv<S>(f + q * P + c) * sc.s[q];
+        const float v = ldv<S>(f + q * P + c) * sc + inc_at(inc, q, x, y, z);
         if (PL::fam(q) == 0) D[PL::comp(q)] += v;
         else B[PL::comp(q)] += v;
     }
@@ -250,15 +286,16 @@ __device__ __forceinline__ void cell_DB(const S *f, const ScaleTab &sc, long lon
 
 // One field component per launch: comp 0..2 -> E_x..E_z, 3..5 -> H_x..H_z.
 template <int MODE, class S>
-__global__ void fields_kernel(const S *f, const float *inv_eps, ScaleTab sc, long long P, int nx,
-                              long long ncell, int nxp, int comp, float *out)
+__global__ void fields_kernel(const S *f, const float *inv_eps, float sc, long long P, int nx,
+                              int ny, long long ncell, int nxp, IncView inc, int comp, float *out)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % nx);
-        const long long c = (i / nx) * nxp + x;
+        const long long r = i / nx;
+        const long long c = r * nxp + x;
         float D[3], B[3];
-        cell_DB<MODE, S>(f, sc, P, c, D, B);
+        cell_DB<MODE, S>(f, sc, P, c, inc, x, (int)(r % ny), (int)(r / ny), D, B);
         out[i] = comp < 3 ? D[comp] * inv_eps[c] : B[comp - 3];
     }
 }
@@ -267,16 +304,18 @@ constexpr int kEThreads = 256;
 
 template <int MODE, class S>
 __global__ void __launch_bounds__(kEThreads) energy_partial(const S *f, const float *inv_eps,
-                                                            ScaleTab sc, long long P, int nx,
-                                                            long long ncell, int nxp, double *partial)
+                                                            float sc, long long P, int nx, int ny,
+                                                            long long ncell, int nxp, IncView inc,
+                                                            double *partial)
 {
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % nx);
-        const long long c = (i / nx) * nxp + x;
+        const long long r = i / nx;
+        const long long c = r * nxp + x;
         float D[3], B[3];
-        cell_DB<MODE, S>(f, sc, P, c, D, B);
+        cell_DB<MODE, S>(f, sc, P, c, inc, x, (int)(r % ny), (int)(r / ny), D, B);
         const double ie = inv_eps[c];
         // 1/2 (eps |E|^2 + |H|^2) = 1/2 (|D|^2 / eps + |B|^2)
         acc += 0.5 * (((double)D[0] * D[0] + (double)D[1] * D[1] + (double)D[2] * D[2]) * ie +
@@ -329,50 +368,73 @@ cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int
 }
 
 cudaError_t launch_pack(int storage, const void *f, long long P, int q, float scale, float *out,
-                        int nx, int ny, int nz, int nxp, cudaStream_t s)
+                        int nx, int ny, int nz, int nxp, const IncView &inc, cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
     const int g = grid_for(n, 256);
-    if (storage == 0) pack_kernel<float><<<g, 256, 0, s>>>((const float *)f + q * P, scale, out, nx, n, nxp);
-    else if (storage == 1) pack_kernel<__half><<<g, 256, 0, s>>>((const __half *)f + q * P, scale, out, nx, n, nxp);
-    else pack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16 *)f + q * P, scale, out, nx, n, nxp);
+    if (storage == 0)
+        pack_kernel<float><<<g, 256, 0, s>>>((const float *)f + q * P, q, scale, out, nx, ny, n, nxp, inc);
+    else if (storage == 1)
+        pack_kernel<__half><<<g, 256, 0, s>>>((const __half *)f + q * P, q, scale, out, nx, ny, n, nxp, inc);
+    else
+        pack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16 *)f + q * P, q, scale, out, nx,
+                                                     ny, n, nxp, inc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(int storage, void *f, long long P, int q, float inv_scale,
-                          const float *in, int nx, int ny, int nz, int nxp, cudaStream_t s)
+                          const float *in, int nx, int ny, int nz, int nxp, const IncView &inc,
+                          cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
     const int g = grid_for(n, 256);
-    if (storage == 0) unpack_kernel<float><<<g, 256, 0, s>>>((float *)f + q * P, inv_scale, in, nx, n, nxp);
-    else if (storage == 1) unpack_kernel<__half><<<g, 256, 0, s>>>((__half *)f + q * P, inv_scale, in, nx, n, nxp);
-    else unpack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)f + q * P, inv_scale, in, nx, n, nxp);
+    if (storage == 0)
+        unpack_kernel<float><<<g, 256, 0, s>>>((float *)f + q * P, q, inv_scale, in, nx, ny, n, nxp, inc);
+    else if (storage == 1)
+        unpack_kernel<__half><<<g, 256, 0, s>>>((__half *)f + q * P, q, inv_scale, in, nx, ny, n, nxp, inc);
+    else
+        unpack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)f + q * P, q, inv_scale, in, nx,
+                                                       ny, n, nxp, inc);
     return cudaGetLastError();
 }
 
-template <int MODE, class S>
-static cudaError_t fields_t(const void *f, const float *inv_eps, const float *scale, long long P,
-                            int nx, int ny, int nz, int nxp, int comp, float *out, cudaStream_t s)
+cudaError_t launch_add_incident(int storage, void *f, long long P, int Q, float scale,
+                                int nx, int ny, int nz, int nxp, const IncView &inc, float sign,
+                                cudaStream_t s)
 {
-    ScaleTab sc;
-    for (int q = 0; q < kMaxQ; ++q) sc.s[q] = scale[q];
     const long long n = (long long)nx * ny * nz;
-    fields_kernel<MODE, S><<<grid_for(n, 256), 256, 0, s>>>((const S *)f, inv_eps, sc, P, nx, n, nxp,
-                                                             comp, out);
+    const int g = grid_for(n, 256);
+    if (storage == 0)
+        add_incident_kernel<float><<<g, 256, 0, s>>>((float *)f, P, Q, scale, nx, ny, n, nxp, inc, sign);
+    else if (storage == 1)
+        add_incident_kernel<__half><<<g, 256, 0, s>>>((__half *)f, P, Q, scale, nx, ny, n, nxp, inc, sign);
+    else
+        add_incident_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)f, P, Q, scale, nx, ny, n,
+                                                             nxp, inc, sign);
     return cudaGetLastError();
 }
 
 template <int MODE, class S>
-static cudaError_t energy_t(const void *f, const float *inv_eps, const float *scale, long long P,
-                            int nx, int ny, int nz, int nxp, double *partial, int max_partial,
-                            double *out, cudaStream_t s)
+static cudaError_t fields_t(const void *f, const float *inv_eps, float sc, long long P,
+                            int nx, int ny, int nz, int nxp, const IncView &inc, int comp,
+                            float *out, cudaStream_t s)
 {
-    ScaleTab sc;
-    for (int q = 0; q < kMaxQ; ++q) sc.s[q] = scale[q];
+    const long long n = (long long)nx * ny * nz;
+    fields_kernel<MODE, S><<<grid_for(n, 256), 256, 0, s>>>((const S *)f, inv_eps, sc, P, nx, ny, n,
+                                                             nxp, inc, comp, out);
+    return cudaGetLastError();
+}
+
+template <int MODE, class S>
+static cudaError_t energy_t(const void *f, const float *inv_eps, float sc, long long P,
+                            int nx, int ny, int nz, int nxp, const IncView &inc, double *partial,
+                            int max_partial, double *out, cudaStream_t s)
+{
     const long long n = (long long)nx * ny * nz;
     int g = grid_for(n, kEThreads);
     if (g > max_partial) g = max_partial;
-    energy_partial<MODE, S><<<g, kEThreads, 0, s>>>((const S *)f, inv_eps, sc, P, nx, n, nxp, partial);
+    energy_partial<MODE, S><<<g, kEThreads, 0, s>>>((const S *)f, inv_eps, sc, P, nx, ny, n, nxp, inc,
+                                                     partial);
     sum_partials<<<1, 32, 0, s>>>(partial, g, out);
     return cudaGetLastError();
 }
@@ -392,19 +454,19 @@ static cudaError_t energy_t(const void *f, const float *inv_eps, const float *sc
     }
 
 cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps,
-                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
-                          int comp, float *out, cudaStream_t s)
+                          float scale, long long P, int nx, int ny, int nz, int nxp,
+                          const IncView &inc, int comp, float *out, cudaStream_t s)
 {
-    LBEM_DISPATCH(fields_t, f, inv_eps, scale, P, nx, ny, nz, nxp, comp, out, s)
+    LBEM_DISPATCH(fields_t, f, inv_eps, scale, P, nx, ny, nz, nxp, inc, comp, out, s)
 }
 
 cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps,
-                          const float *scale, long long P, int nx, int ny, int nz, int nxp,
-                          double *partial, int max_partial, double *out, cudaStream_t s,
-                          int *launches)
+                          float scale, long long P, int nx, int ny, int nz, int nxp,
+                          const IncView &inc, double *partial, int max_partial, double *out,
+                          cudaStream_t s, int *launches)
 {
     if (launches) *launches += 2;
-    LBEM_DISPATCH(energy_t, f, inv_eps, scale, P, nx, ny, nz, nxp, partial, max_partial, out, s)
+    LBEM_DISPATCH(energy_t, f, inv_eps, scale, P, nx, ny, nz, nxp, inc, partial, max_partial, out, s)
 }
 
 }  // namespace lbem

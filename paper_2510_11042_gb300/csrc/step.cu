@@ -1,18 +1,43 @@
 // Fused D3Q7 stream-and-collide step for the lattice-Boltzmann Maxwell scheme
 // of arXiv 2510.11042, Sec. 2.1 (Eqs. 1-2) with the outer boundary of Eq. 4.
 //
-// One launch advances every cell by one time step and, in one extra block,
-// the 1D incident line that feeds the total-field/scattered-field links:
+// One launch advances every cell by one time step:
 //   pull    f_i(r) = f*_i(clamp(r - c_i))           (Eq. 1 streaming + Eq. 4)
-//   TF/SF   +/- incident f*_i of the link's source cell on links crossing the box
+//   TF/SF   incident population of the link's source cell added on links that
+//           enter the total-field box, removed on links that leave it
 //   moments D = sum_i e_i, B = sum_i h_i, E = D / eps_r, H = B  (mu_r = 1)
 //   DFT     X += x(t) exp(-j w t) on the NTFF box surface (FP64 accumulators)
 //   collide f* = 2 f_eq - f (tau = 1/2, equilibria of Eq. 2):
 //             e_0* = 2 (eps_r - 1) E - e_0 = 2 (D - E) - e_0
 //             e_i* = (E - c_i x H) / 3 - e_i,    h_0* = -h_0,
 //             h_i* = (H + c_i x E) / 3 - h_i
+//           with E/3 and H/3 free of rounding bias, so that the sum of the moving
+//           equilibria, 6 (E/3), carries no systematic rounding bias and D, B
+//           are conserved to unbiased rounding;
 //   layer   f* *= 1 - sigma_max (m / W)^3 near the outer faces
 //   store   to the other ping-pong buffer.
+//
+// Scattered-field storage.  Inside the total-field box the kernel stores
+// G = F - I, the total post-collision population minus the incident one of
+// the 1D incident line at the same time and coordinate along k; outside the
+// box G = F (there the field is the scattered one).  The link-wise TF/SF rule
+// (I added on links entering the box, removed on links leaving it) then reads
+// F(r) = G(src) + chi(r) I(src) for every pull, and, C_eps being the linear
+// collision of a cell,
+//     G*(r) = C_eps(G_pulled) + chi(r) [C_eps(I_pulled) - I(r, n+1)].
+// Inside the box the line is the vacuum update, I(r, n+1) = C_1(I_pulled), so
+// the bracket is (C_eps - C_1)(I_pulled): zero in vacuum cells and, in a
+// dielectric cell, the equilibrium of the field dE = E_inc (1/eps_r - 1) with
+// no magnetic part (e_0: -2 dE, e_i: dE/3, h_i: c_i x dE/3), where E_inc is
+// the line's field at time n+1.  So every cell runs the plain update on G and
+// only dielectric cells inside the box add that source.  The stored values are
+// scattered fields everywhere, which keeps reduced-precision storage errors
+// proportional to the scattered field rather than to the incident one.
+//
+// The incident line (same update, eps_r = 1, absorbing layer at both ends,
+// hard source) runs one step ahead of the lattice in three rotating buffers:
+// during step n the lattice reads line(n+1) and the first blocks of the same
+// launch write line(n+2).
 //
 // Memory layout: structure of arrays, one plane per (family, direction,
 // component) of nz*ny*nxp elements, x fastest and padded to a multiple of
@@ -40,6 +65,17 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16>(__nv_bfloat16 *p, 
     *p = __float2bfloat16_rn(v);
 }
 
+// x/3 to within rounding: the constant 1/3 split into a float and a remainder,
+// x*hi + x*lo evaluated with one rounding (FMA).  A plain x * fl(1/3) is biased
+// upwards (fl(1/3) > 1/3), which would make the collision grow D and B by
+// ~2e-8 per step; this form is unbiased.
+__device__ __forceinline__ float third(float x)
+{
+    constexpr float hi = 0.333333343267f;        // fl(1/3)
+    constexpr float lo = -9.934107481e-09f;      // 1/3 - fl(1/3)
+    return fmaf(x, hi, x * lo);
+}
+
 // Direction i = 0..6: rest, +x, -x, +y, -y, +z, -z.
 __host__ __device__ constexpr int dir_axis(int i) { return i == 0 ? -1 : (i - 1) / 2; }
 __host__ __device__ constexpr int dir_sign(int i) { return i == 0 ? 0 : ((i & 1) ? 1 : -1); }
@@ -55,7 +91,6 @@ __device__ __forceinline__ float cross_c(int i, const float V[3], int a)
     return a == 0 ? -s * V[1] : (a == 1 ? s * V[0] : 0.f);
 }
 
-// Moments, collision and equilibrium for one cell held in registers.
 template <int MODE>
 __device__ __forceinline__ void moments(const float *f, float inv_eps, float D[3], float E[3],
                                         float H[3])
@@ -75,36 +110,28 @@ __device__ __forceinline__ void moments(const float *f, float inv_eps, float D[3
     }
 }
 
+// f <- 2 f_eq - f.  2 e_i^eq = (E - c_i x H)/3 = E/3 - c_i x (H/3) for i != 0.
 template <int MODE>
 __device__ __forceinline__ void collide(float *f, const float D[3], const float E[3],
                                         const float H[3])
 {
     using PL = Planes<MODE>;
-    constexpr float third = 1.0f / 3.0f;
+    using M = Mode<MODE>;
+    float E3[3] = {0.f, 0.f, 0.f}, H3[3] = {0.f, 0.f, 0.f};
+    // only the components the mode carries are non-zero
+#pragma unroll
+    for (int k = 0; k < PL::NE; ++k) E3[M::ec(k)] = third(E[M::ec(k)]);
+#pragma unroll
+    for (int k = 0; k < PL::NH; ++k) H3[M::hc(k)] = third(H[M::hc(k)]);
 #pragma unroll
     for (int q = 0; q < PL::Q; ++q) {
         const int i = PL::dir(q), a = PL::comp(q);
         float eq2;  // 2 f_eq
         if (PL::fam(q) == 0)
-            eq2 = (i == 0) ? 2.f * (D[a] - E[a]) : (E[a] - cross_c(i, H, a)) * third;
+            eq2 = (i == 0) ? 2.f * (D[a] - E[a]) : E3[a] - cross_c(i, H3, a);
         else
-            eq2 = (i == 0) ? 0.f : (H[a] + cross_c(i, E, a)) * third;
+            eq2 = (i == 0) ? 0.f : H3[a] + cross_c(i, E3, a);
         f[q] = eq2 - f[q];
-    }
-}
-
-// Vacuum equilibrium of prescribed fields (hard source of the incident line).
-template <int MODE>
-__device__ __forceinline__ void vacuum_equilibrium(float *f, const float E[3], const float H[3])
-{
-    using PL = Planes<MODE>;
-    constexpr float sixth = 1.0f / 6.0f;
-#pragma unroll
-    for (int q = 0; q < PL::Q; ++q) {
-        const int i = PL::dir(q), a = PL::comp(q);
-        if (i == 0) f[q] = 0.f;
-        else if (PL::fam(q) == 0) f[q] = (E[a] - cross_c(i, H, a)) * sixth;
-        else f[q] = (H[a] + cross_c(i, E, a)) * sixth;
     }
 }
 
@@ -120,108 +147,80 @@ __device__ __forceinline__ bool in_box(int x, int y, int z, const int lo[3], con
     return x >= lo[0] && x <= hi[0] && y >= lo[1] && y <= hi[1] && z >= lo[2] && z <= hi[2];
 }
 
-// The 1D incident line: the same update on an n_line x 1 x 1 lattice along
-// inc_axis (eps_r = 1), absorbing layer at both ends, hard source at src_index.
+// One node s of the incident line: line_out[.][s] = update of line_in at node s
+// (pull along the line with the clamped ends, eps_r = 1 moments and collision,
+// absorbing layer at both ends, hard source overwrite at src_index).
 template <int MODE>
-__device__ void line_update(const StepArgs &a)
+__device__ __noinline__ void line_node(const float *__restrict__ line_in, float *__restrict__ line_out,
+                                       int n, int s, int w, float sigma_max, float inv_w,
+                                       int src_index, float sE0, float sE1, float sE2, float sH0,
+                                       float sH1, float sH2, int axis)
 {
     using PL = Planes<MODE>;
     constexpr int Q = PL::Q;
-    const int n = a.n_line, ax = a.inc_axis;
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        float f[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int i = PL::dir(q);
-            const int c = (dir_axis(i) == ax) ? dir_sign(i) : 0;
-            int src = s - c;
-            src = src < 0 ? 0 : (src > n - 1 ? n - 1 : src);
-            f[q] = a.line_in[(size_t)q * n + src];
-        }
-        float D[3], E[3], H[3];
-        moments<MODE>(f, 1.f, D, E, H);
-        if (a.dft_on) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double v = a.dft_scale * (double)E[c];
-                a.line_dft[(s * 3 + c) * 2 + 0] += v * a.dft_c;
-                a.line_dft[(s * 3 + c) * 2 + 1] -= v * a.dft_s;
-            }
-        }
-        collide<MODE>(f, D, E, H);
-        const int d = min(s, n - 1 - s);
-        const float keep = layer_keep(d, a.w, a.sigma_max, a.inv_w);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) f[q] *= keep;
-        if (s == a.src_index) vacuum_equilibrium<MODE>(f, a.src_E, a.src_H);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) a.line_out[(size_t)q * n + s] = f[q];
-    }
-}
-
-template <int MODE, class S, int BX>
-__global__ void __launch_bounds__(BX) step_kernel(const StepArgs a)
-{
-    using PL = Planes<MODE>;
-    constexpr int Q = PL::Q;
-    constexpr bool kScaled = !std::is_same<S, float>::value;
-    const int b = blockIdx.x;
-    if (b >= a.nblk_main) {
-        if (a.line_on) line_update<MODE>(a);
-        return;
-    }
-    const int bx = b % a.nblk_x;
-    const int row = b / a.nblk_x;
-    const int y = row % a.ny;
-    const int z = row / a.ny;
-    const int x = bx * BX + threadIdx.x;
-    if (x >= a.nx) return;
-
-    const int pz = a.ny * a.nxp;
-    const int c = z * pz + y * a.nxp + x;
-    int src[7];
-    src[0] = c;
-    src[1] = c - (x > 0 ? 1 : 0);
-    src[2] = c + (x < a.nx - 1 ? 1 : 0);
-    src[3] = c - (y > 0 ? a.nxp : 0);
-    src[4] = c + (y < a.ny - 1 ? a.nxp : 0);
-    src[5] = c - (z > 0 ? pz : 0);
-    src[6] = c + (z < a.nz - 1 ? pz : 0);
-
-    const S *fin = static_cast<const S *>(a.fin);
     float f[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        f[q] = ld<S>(fin + (size_t)q * a.P + src[PL::dir(q)]);
-        if (kScaled) f[q] *= a.scale[q];
+        const int i = PL::dir(q);
+        const int c = (dir_axis(i) == axis) ? dir_sign(i) : 0;
+        int src = s - c;
+        src = src < 0 ? 0 : (src > n - 1 ? n - 1 : src);
+        f[q] = line_in[(size_t)q * n + src];
     }
-    const float inv_eps = __ldg(a.inv_eps + c);
-
-    // TF/SF: only cells within one cell of the total-field box surface.
-    if (a.tfsf) {
-        const bool near = x >= a.tf_lo[0] - 1 && x <= a.tf_hi[0] + 1 && y >= a.tf_lo[1] - 1 &&
-                          y <= a.tf_hi[1] + 1 && z >= a.tf_lo[2] - 1 && z <= a.tf_hi[2] + 1;
-        if (near) {
-            const bool in_r = in_box(x, y, z, a.tf_lo, a.tf_hi);
+    float D[3], E[3], H[3];
+    moments<MODE>(f, 1.f, D, E, H);
+    collide<MODE>(f, D, E, H);
+    const float keep = layer_keep(min(s, n - 1 - s), w, sigma_max, inv_w);
 #pragma unroll
-            for (int i = 1; i < 7; ++i) {
-                const int d = dir_axis(i), sg = dir_sign(i);
-                int sx = x, sy = y, sz = z;
-                if (d == 0) sx = min(max(x - sg, 0), a.nx - 1);
-                if (d == 1) sy = min(max(y - sg, 0), a.ny - 1);
-                if (d == 2) sz = min(max(z - sg, 0), a.nz - 1);
-                const bool in_s = in_box(sx, sy, sz, a.tf_lo, a.tf_hi);
-                if (in_r != in_s) {
-                    const float sign = in_r ? 1.f : -1.f;
-                    const int sa = a.inc_axis == 0 ? sx : (a.inc_axis == 1 ? sy : sz);
+    for (int q = 0; q < Q; ++q) f[q] *= keep;
+    if (s == src_index) {
+        // vacuum equilibrium of the prescribed incident fields
+        const float sE[3] = {sE0, sE1, sE2}, sH[3] = {sH0, sH1, sH2};
+        constexpr float sixth = 1.0f / 6.0f;
 #pragma unroll
-                    for (int q = 0; q < Q; ++q)
-                        if (PL::dir(q) == i) f[q] += sign * a.inc[(size_t)q * a.n_line + sa];
-                }
-            }
+        for (int q = 0; q < Q; ++q) {
+            const int i = PL::dir(q), a = PL::comp(q);
+            if (i == 0) f[q] = 0.f;
+            else if (PL::fam(q) == 0) f[q] = (sE[a] - cross_c(i, sH, a)) * sixth;
+            else f[q] = (sH[a] + cross_c(i, sE, a)) * sixth;
         }
     }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) line_out[(size_t)q * n + s] = f[q];
+}
 
+// Line work done by the first blocks of a step: DFT of the line's fields at
+// time n+1 (moments of the stored state, conserved by collision) and the
+// update line(n+1) -> line(n+2).
+template <int MODE>
+__device__ __forceinline__ void line_work(const StepArgs &a, int s)
+{
+    using PL = Planes<MODE>;
+    const int n = a.n_line;
+    if (a.dft_on) {
+        float E[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 7 * PL::NE; ++q) E[PL::comp(q)] += a.line_n1[(size_t)q * n + s];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double v = a.dft_scale * (double)E[c];
+            a.line_dft[(s * 3 + c) * 2 + 0] += v * a.dft_c;
+            a.line_dft[(s * 3 + c) * 2 + 1] -= v * a.dft_s;
+        }
+    }
+    line_node<MODE>(a.line_n1, a.line_out, n, s, a.w, a.sigma_max, a.inv_w, a.src_index,
+                    a.src_E[0], a.src_E[1], a.src_E[2], a.src_H[0], a.src_H[1], a.src_H[2],
+                    a.inc_axis);
+}
+
+// Moments, DFT, collision, absorbing layer and incident source of one cell
+// whose pulled populations are in f; leaves the post-collision values in f.
+template <int MODE>
+__device__ __forceinline__ void update_cell(float *f, int x, int y, int z, float inv_eps,
+                                            const StepArgs &a)
+{
+    using PL = Planes<MODE>;
+    constexpr int Q = PL::Q;
     float D[3], E[3], H[3];
     moments<MODE>(f, inv_eps, D, E, H);
 
@@ -245,7 +244,7 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs a)
                 const long long plane = (long long)nu * nv;
 #pragma unroll
                 for (int k = 0; k < PL::NC; ++k) {
-                    const double v = a.dft_scale * (double)vals[k];
+                    const double v = a.dft_scale_cells * (double)vals[k];
                     base[(2 * k + 0) * plane] += v * a.dft_c;
                     base[(2 * k + 1) * plane] -= v * a.dft_s;
                 }
@@ -260,31 +259,106 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs a)
     if (a.nz > 1) d = min(d, min(z, a.nz - 1 - z));
     const float keep = layer_keep(d, a.w, a.sigma_max, a.inv_w);
 
-    S *fout = static_cast<S *>(a.fout);
+    // incident-field source of dielectric cells inside the total-field box
+    // (the box lies outside the absorbing layer, so keep == 1 there)
+    if (a.tfsf && inv_eps != 1.0f && in_box(x, y, z, a.tf_lo, a.tf_hi)) {
+        const int sl = a.inc_axis == 0 ? x : (a.inc_axis == 1 ? y : z);
+        float dE[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        float v = f[q] * keep;
-        if (kScaled) v *= a.inv_scale[q];
-        st<S>(fout + (size_t)q * a.P + c, v);
+        for (int q = 0; q < 7 * PL::NE; ++q)
+            dE[PL::comp(q)] += __ldg(a.line_n1 + (size_t)q * a.n_line + sl);
+        const float g = (inv_eps - 1.0f) * a.inv_scale;  // to storage units
+        float dE3[3];
+#pragma unroll
+        for (int c3 = 0; c3 < 3; ++c3) {
+            dE[c3] *= g;
+            dE3[c3] = third(dE[c3]);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int i = PL::dir(q), ac = PL::comp(q);
+            if (PL::fam(q) == 0) f[q] += (i == 0) ? -2.f * dE[ac] : dE3[ac];
+            else if (i != 0) f[q] += cross_c(i, dE3, ac);
+        }
     }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] *= keep;
+}
+
+// One thread per cell of a row.  Plane q of the input/output buffers starts
+// at a.fin_q[q] / a.fout_q[q] (kernel parameters), so every access is a 32-bit
+// in-plane offset from a constant-bank base.  Reduced-precision storage holds
+// populations divided by one power-of-two scale s shared by all planes; the
+// update is linear and homogeneous, so it runs directly in those units and
+// only the DFT (fields times s) and the incident source (divided by s) convert.
+template <int MODE, class S, int BX>
+__global__ void __launch_bounds__(BX) step_kernel(const StepArgs a)
+{
+    using PL = Planes<MODE>;
+    constexpr int Q = PL::Q;
+    const int b = blockIdx.x;
+    if (a.line_on) {
+        const int s = b * BX + threadIdx.x;
+        if (s < a.n_line) line_work<MODE>(a, s);
+    }
+    const int bx = b % a.nblk_x;
+    const int row = b / a.nblk_x;
+    const int y = row % a.ny;
+    const int z = row / a.ny;
+    const int x = bx * BX + threadIdx.x;
+    if (x >= a.nx) return;
+
+    const int pz = a.ny * a.nxp;
+    const int c = z * pz + y * a.nxp + x;
+    int src[7];
+    src[0] = c;
+    src[1] = c - (x > 0 ? 1 : 0);
+    src[2] = c + (x < a.nx - 1 ? 1 : 0);
+    src[3] = c - (y > 0 ? a.nxp : 0);
+    src[4] = c + (y < a.ny - 1 ? a.nxp : 0);
+    src[5] = c - (z > 0 ? pz : 0);
+    src[6] = c + (z < a.nz - 1 ? pz : 0);
+
+    float f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = ld<S>(static_cast<const S *>(a.fin_q[q]) + src[PL::dir(q)]);
+    const float inv_eps = __ldg(a.inv_eps + c);
+
+    update_cell<MODE>(f, x, y, z, inv_eps, a);
+
+#pragma unroll
+    for (int q = 0; q < Q; ++q) st<S>(static_cast<S *>(a.fout_q[q]) + c, f[q]);
+}
+
+// First update of a freshly started incident line: line(t+1) from line(t).
+template <int MODE>
+__global__ void line_init_kernel(const StepArgs a)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < a.n_line)
+        line_node<MODE>(a.line_n, a.line_out, a.n_line, s, a.w, a.sigma_max, a.inv_w, a.src_index,
+                        a.src_E[0], a.src_E[1], a.src_E[2], a.src_H[0], a.src_H[1], a.src_H[2],
+                        a.inc_axis);
 }
 
 constexpr int kBX = 128;
+constexpr int kCellsPerThread = 1;
 
 template <int MODE, class S>
 cudaError_t launch_t(const StepArgs &a, cudaStream_t s)
 {
-    const int nblk = a.nblk_main + (a.line_on ? 1 : 0);
-    step_kernel<MODE, S, kBX><<<nblk, kBX, 0, s>>>(a);
+    step_kernel<MODE, S, kBX><<<a.nblk_main, kBX, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int step_block_x() { return kBX; }
+int step_cells_per_block() { return kBX * kCellsPerThread; }
+int step_block_threads() { return kBX; }
 
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s)
 {
+    if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
     switch (mode * 3 + storage) {
     case 0: return launch_t<0, float>(a, s);
     case 1: return launch_t<0, __half>(a, s);
@@ -297,6 +371,18 @@ cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s
     case 8: return launch_t<2, __nv_bfloat16>(a, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_line_init(int mode, const StepArgs &a, cudaStream_t s)
+{
+    const int blocks = (a.n_line + 127) / 128;
+    switch (mode) {
+    case 0: line_init_kernel<0><<<blocks, 128, 0, s>>>(a); break;
+    case 1: line_init_kernel<1><<<blocks, 128, 0, s>>>(a); break;
+    case 2: line_init_kernel<2><<<blocks, 128, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace lbem

@@ -73,8 +73,8 @@ _SIGS = {
     "lbem_state_bytes": (_I32, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "lbem_save_state": (_I32, [_P, _P, ctypes.c_size_t]),
     "lbem_load_state": (_I32, [_P, _P, ctypes.c_size_t]),
-    "lbem_set_storage_scales": (_I32, [_P, _P]),
-    "lbem_get_storage_scales": (_I32, [_P, _P]),
+    "lbem_set_storage_scale": (_I32, [_P, ctypes.c_float]),
+    "lbem_get_storage_scale": (_I32, [_P, ctypes.POINTER(ctypes.c_float)]),
     "lbem_sync": (_I32, [_P]),
     "lbem_destroy": (None, [_P]),
     "lbem_last_error": (ctypes.c_char_p, [_P]),
@@ -259,15 +259,14 @@ def lbem_load_state(h, buf: np.ndarray):
     _check(lib().lbem_load_state(h, buf.ctypes.data, buf.size), h)
 
 
-def lbem_set_storage_scales(h, scales):
-    s = np.ascontiguousarray(scales, np.float32)
-    _check(lib().lbem_set_storage_scales(h, s.ctypes.data), h)
+def lbem_set_storage_scale(h, scale: float):
+    _check(lib().lbem_set_storage_scale(h, float(scale)), h)
 
 
-def lbem_get_storage_scales(h, q: int) -> np.ndarray:
-    s = np.zeros(42, np.float32)
-    _check(lib().lbem_get_storage_scales(h, s.ctypes.data), h)
-    return s[:q]
+def lbem_get_storage_scale(h) -> float:
+    v = ctypes.c_float()
+    _check(lib().lbem_get_storage_scale(h, ctypes.byref(v)), h)
+    return v.value
 
 
 def lbem_sync(h):
