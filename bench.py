@@ -58,10 +58,14 @@ def b_cell(mode: str, storage: str) -> int:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the step kernel's source: step.cu and the StepArgs definition."""
+    csrc = os.path.join(ROOT, "paper_2510_11042_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("step.cu", "lbem_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2510_11042_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "step.cu"), "rb") as fh:
+        h.update(fh.read())
+    hdr = open(os.path.join(csrc, "lbem_internal.cuh")).read()
+    i = hdr.index("struct StepArgs {")
+    h.update(hdr[i:hdr.index("};", i)].encode())
     return h.hexdigest()[:16]
 
 

@@ -11,10 +11,6 @@
 #include "../../include/lbem.h"
 #include "lbem_internal.cuh"
 
-namespace lbem {
-int step_cells_per_block();
-}
-
 using namespace lbem;
 
 struct lbem_ctx {
@@ -80,6 +76,16 @@ static int cuda_fail(lbem_ctx *h, cudaError_t e, const char *what)
         cudaError_t e_ = (call);                                  \
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
     } while (0)
+
+// Kernel status word: a step kernel that gave up on a bounded wait sets bit 0.
+static int check_status(lbem_ctx *h)
+{
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (st & 1) return fail(h, LBEM_ERR_TIMEOUT, "a step kernel gave up waiting for its staged copies");
+    return LBEM_OK;
+}
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -196,17 +202,15 @@ static IncView inc_view(lbem_ctx *h)
 static void fill_common_args(lbem_ctx *h, StepArgs &a)
 {
     std::memset(&a, 0, sizeof a);
-    const int BX = step_cells_per_block();
     a.inv_eps = h->inv_eps;
     a.nx = h->g.nx; a.ny = h->g.ny; a.nz = h->g.nz; a.nxp = h->nxp;
     a.P = h->P;
-    a.nblk_x = (h->g.nx + BX - 1) / BX;
-    a.nblk_main = a.nblk_x * h->g.ny * h->g.nz;
     a.w = h->g.absorber_width;
     a.sigma_max = (float)h->g.sigma_max;
     a.inv_w = a.w > 0 ? 1.0f / (float)a.w : 0.f;
     a.scale = h->scale;
     a.inv_scale = h->inv_scale;
+    a.status = h->flag + 1;
     if (!h->has_wave) return;
     a.tfsf = 1;
     a.line_on = 1;
@@ -318,7 +322,8 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->flag = (int *)(h->ws + L.flag);
     default_scale(h);
     int rc = LBEM_OK;
-    cudaError_t e = cudaMemsetAsync(h->f[0], 0, (size_t)L.Q * L.P * L.elem, h->stream);
+    cudaError_t e = cudaMemsetAsync(h->flag, 0, 256, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, (size_t)L.Q * L.P * L.elem, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, (size_t)L.Q * L.P * L.elem, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->inv_eps, 0, (size_t)L.P * 4, h->stream);
     if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaMemsetAsync");
@@ -674,7 +679,7 @@ int32_t lbem_energy(lbem_handle h, double *out)
     CK(h, cudaMemcpyAsync(out, d_out, 8, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (!std::isfinite(*out)) return fail(h, LBEM_ERR_NONFINITE, "non-finite population in the state");
-    return LBEM_OK;
+    return check_status(h);
 }
 
 // checkpoint: header | populations | incident line | line DFT | face DFT
@@ -789,7 +794,7 @@ int32_t lbem_sync(lbem_handle h)
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
     CK(h, cudaStreamSynchronize(h->stream));
     CK(h, cudaGetLastError());
-    return LBEM_OK;
+    return check_status(h);
 }
 
 void lbem_destroy(lbem_handle h)

@@ -58,8 +58,10 @@ struct StepArgs {
     const float *inv_eps;
     int nx, ny, nz, nxp;       // extent and padded row pitch (elements)
     long long P;               // plane stride in elements = nz*ny*nxp
-    int nblk_x;                // blocks per row
-    int nblk_main;             // blocks covering the lattice
+    int nblk_x;                // blocks per row (set by the launcher)
+    int rows_per_block;        // rows (y fastest, then z) per block (launcher)
+    int nblk_main;             // blocks covering the lattice (set by the launcher)
+    int *status;               // kernel error flags (bit 0: a bounded wait ran out)
     // absorbing layer
     int w;
     float sigma_max, inv_w;

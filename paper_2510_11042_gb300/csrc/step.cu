@@ -52,19 +52,6 @@
 namespace lbem {
 namespace {
 
-template <class S> __device__ __forceinline__ float ld(const S *p);
-template <> __device__ __forceinline__ float ld<float>(const float *p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ld<__half>(const __half *p) { return __half2float(__ldg(p)); }
-template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16 *p) {
-    return __bfloat162float(__ldg(p));
-}
-template <class S> __device__ __forceinline__ void st(S *p, float v);
-template <> __device__ __forceinline__ void st<float>(float *p, float v) { *p = v; }
-template <> __device__ __forceinline__ void st<__half>(__half *p, float v) { *p = __float2half_rn(v); }
-template <> __device__ __forceinline__ void st<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
-    *p = __float2bfloat16_rn(v);
-}
-
 // x/3 to within rounding: the constant 1/3 split into a float and a remainder,
 // x*hi + x*lo evaluated with one rounding (FMA).  A plain x * fl(1/3) is biased
 // upwards (fl(1/3) > 1/3), which would make the collision grow D and B by
@@ -213,25 +200,44 @@ __device__ __forceinline__ void line_work(const StepArgs &a, int s)
                     a.inc_axis);
 }
 
-// Moments, DFT, collision, absorbing layer and incident source of one cell
-// whose pulled populations are in f; leaves the post-collision values in f.
-template <int MODE>
-__device__ __forceinline__ void update_cell(float *f, int x, int y, int z, float inv_eps,
+// Accessor of one cell's pulled populations held in registers.
+struct FloatCell {
+    float *f;
+    __device__ __forceinline__ float get(int q) const { return f[q]; }
+    __device__ __forceinline__ void set(int q, float v) { f[q] = v; }
+};
+
+// Moments, DFT, collision, incident source and absorbing layer of one cell,
+// in one pass over its populations after the moments:
+//   f* = (2 f_eq - f + source) * keep.
+// Values are in storage units (population / scale); fields go to the DFT
+// multiplied back by the scale (dft_scale_cells), the incident source is
+// divided by it.
+template <int MODE, class Cell>
+__device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float inv_eps,
                                             const StepArgs &a)
 {
     using PL = Planes<MODE>;
+    using M = Mode<MODE>;
     constexpr int Q = PL::Q;
-    float D[3], E[3], H[3];
-    moments<MODE>(f, inv_eps, D, E, H);
+    float D[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (PL::fam(q) == 0) D[PL::comp(q)] += f.get(q);
+        else B[PL::comp(q)] += f.get(q);
+    }
+    float E[3], E3[3] = {0.f, 0.f, 0.f}, H3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) E[c3] = D[c3] * inv_eps;
 
     if (a.dft_on && in_box(x, y, z, a.nt_lo, a.nt_hi)) {
         const int g[3] = {x, y, z};
         const int n3[3] = {a.nx, a.ny, a.nz};
         float vals[PL::NC];
 #pragma unroll
-        for (int k = 0; k < PL::NE; ++k) vals[k] = E[Mode<MODE>::ec(k)];
+        for (int k = 0; k < PL::NE; ++k) vals[k] = E[M::ec(k)];
 #pragma unroll
-        for (int k = 0; k < PL::NH; ++k) vals[PL::NE + k] = H[Mode<MODE>::hc(k)];
+        for (int k = 0; k < PL::NH; ++k) vals[PL::NE + k] = B[M::hc(k)];
         int face = 0;
         for (int ax = 0; ax < 3; ++ax) {
             if (n3[ax] <= 1) continue;
@@ -252,7 +258,10 @@ __device__ __forceinline__ void update_cell(float *f, int x, int y, int z, float
         }
     }
 
-    collide<MODE>(f, D, E, H);
+#pragma unroll
+    for (int k = 0; k < PL::NE; ++k) E3[M::ec(k)] = third(E[M::ec(k)]);
+#pragma unroll
+    for (int k = 0; k < PL::NH; ++k) H3[M::hc(k)] = third(B[M::hc(k)]);
 
     int d = min(x, a.nx - 1 - x);
     d = min(d, min(y, a.ny - 1 - y));
@@ -261,38 +270,76 @@ __device__ __forceinline__ void update_cell(float *f, int x, int y, int z, float
 
     // incident-field source of dielectric cells inside the total-field box
     // (the box lies outside the absorbing layer, so keep == 1 there)
-    if (a.tfsf && inv_eps != 1.0f && in_box(x, y, z, a.tf_lo, a.tf_hi)) {
+    const bool source = a.tfsf && inv_eps != 1.0f && in_box(x, y, z, a.tf_lo, a.tf_hi);
+    if (!source && keep == 1.0f) {
+        // most cells: plain collision, f* = 2 f_eq - f
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int i = PL::dir(q), ac = PL::comp(q);
+            float eq2;
+            if (PL::fam(q) == 0) eq2 = (i == 0) ? 2.f * (D[ac] - E[ac]) : E3[ac] - cross_c(i, H3, ac);
+            else eq2 = (i == 0) ? 0.f : H3[ac] + cross_c(i, E3, ac);
+            f.set(q, eq2 - f.get(q));
+        }
+        return;
+    }
+    float dE[3] = {0.f, 0.f, 0.f}, dE3[3] = {0.f, 0.f, 0.f};
+    if (source) {
         const int sl = a.inc_axis == 0 ? x : (a.inc_axis == 1 ? y : z);
-        float dE[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 7 * PL::NE; ++q)
             dE[PL::comp(q)] += __ldg(a.line_n1 + (size_t)q * a.n_line + sl);
         const float g = (inv_eps - 1.0f) * a.inv_scale;  // to storage units
-        float dE3[3];
 #pragma unroll
         for (int c3 = 0; c3 < 3; ++c3) {
             dE[c3] *= g;
             dE3[c3] = third(dE[c3]);
         }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int i = PL::dir(q), ac = PL::comp(q);
-            if (PL::fam(q) == 0) f[q] += (i == 0) ? -2.f * dE[ac] : dE3[ac];
-            else if (i != 0) f[q] += cross_c(i, dE3, ac);
-        }
     }
+
 #pragma unroll
-    for (int q = 0; q < Q; ++q) f[q] *= keep;
+    for (int q = 0; q < Q; ++q) {
+        const int i = PL::dir(q), ac = PL::comp(q);
+        float eq2, src;  // 2 f_eq and the incident source
+        if (PL::fam(q) == 0) {
+            eq2 = (i == 0) ? 2.f * (D[ac] - E[ac]) : E3[ac] - cross_c(i, H3, ac);
+            src = (i == 0) ? -2.f * dE[ac] : dE3[ac];
+        } else {
+            eq2 = (i == 0) ? 0.f : H3[ac] + cross_c(i, E3, ac);
+            src = (i == 0) ? 0.f : cross_c(i, dE3, ac);
+        }
+        f.set(q, (eq2 - f.get(q) + src) * keep);
+    }
+}
+
+__device__ __forceinline__ void block_row(const StepArgs &a, int b, int &x_block, int &y, int &z)
+{
+    x_block = b % a.nblk_x;
+    const int row = b / a.nblk_x;
+    y = row % a.ny;
+    z = row / a.ny;
+}
+
+template <class S> __device__ __forceinline__ float load_pop(const S *p);
+template <> __device__ __forceinline__ float load_pop<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_pop<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <> __device__ __forceinline__ float load_pop<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <class S> __device__ __forceinline__ void store_pop(S *p, float v);
+template <> __device__ __forceinline__ void store_pop<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void store_pop<__half>(__half *p, float v) { *p = __float2half_rn(v); }
+template <> __device__ __forceinline__ void store_pop<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
 }
 
 // One thread per cell of a row.  Plane q of the input/output buffers starts
-// at a.fin_q[q] / a.fout_q[q] (kernel parameters), so every access is a 32-bit
-// in-plane offset from a constant-bank base.  Reduced-precision storage holds
-// populations divided by one power-of-two scale s shared by all planes; the
-// update is linear and homogeneous, so it runs directly in those units and
-// only the DFT (fields times s) and the incident source (divided by s) convert.
+// at a.fin_q[q] / a.fout_q[q] (kernel parameters), so every access is a
+// 32-bit in-plane offset from a constant-bank base; the +-x pulls are plain
+// loads shifted by one element (coalesced; the extra sector per warp hits in
+// L1/L2).
 template <int MODE, class S, int BX>
-__global__ void __launch_bounds__(BX) step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(BX, sizeof(S) == 4 ? 6 : 7) step_kernel_cell(const StepArgs a)
 {
     using PL = Planes<MODE>;
     constexpr int Q = PL::Q;
@@ -301,10 +348,8 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs a)
         const int s = b * BX + threadIdx.x;
         if (s < a.n_line) line_work<MODE>(a, s);
     }
-    const int bx = b % a.nblk_x;
-    const int row = b / a.nblk_x;
-    const int y = row % a.ny;
-    const int z = row / a.ny;
+    int bx, y, z;
+    block_row(a, b, bx, y, z);
     const int x = bx * BX + threadIdx.x;
     if (x >= a.nx) return;
 
@@ -321,13 +366,11 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs a)
 
     float f[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) f[q] = ld<S>(static_cast<const S *>(a.fin_q[q]) + src[PL::dir(q)]);
-    const float inv_eps = __ldg(a.inv_eps + c);
-
-    update_cell<MODE>(f, x, y, z, inv_eps, a);
-
+    for (int q = 0; q < Q; ++q) f[q] = load_pop<S>(static_cast<const S *>(a.fin_q[q]) + src[PL::dir(q)]);
+    FloatCell cell{f};
+    update_cell<MODE>(cell, x, y, z, __ldg(a.inv_eps + c), a);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) st<S>(static_cast<S *>(a.fout_q[q]) + c, f[q]);
+    for (int q = 0; q < Q; ++q) store_pop<S>(static_cast<S *>(a.fout_q[q]) + c, f[q]);
 }
 
 // First update of a freshly started incident line: line(t+1) from line(t).
@@ -342,33 +385,31 @@ __global__ void line_init_kernel(const StepArgs a)
 }
 
 constexpr int kBX = 128;
-constexpr int kCellsPerThread = 1;
 
 template <int MODE, class S>
-cudaError_t launch_t(const StepArgs &a, cudaStream_t s)
+cudaError_t launch_cell(StepArgs a, cudaStream_t s)
 {
-    step_kernel<MODE, S, kBX><<<a.nblk_main, kBX, 0, s>>>(a);
+    a.nblk_x = (a.nx + kBX - 1) / kBX;
+    a.nblk_main = a.nblk_x * a.ny * a.nz;
+    if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
+    step_kernel_cell<MODE, S, kBX><<<a.nblk_main, kBX, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int step_cells_per_block() { return kBX * kCellsPerThread; }
-int step_block_threads() { return kBX; }
-
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s)
 {
-    if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
     switch (mode * 3 + storage) {
-    case 0: return launch_t<0, float>(a, s);
-    case 1: return launch_t<0, __half>(a, s);
-    case 2: return launch_t<0, __nv_bfloat16>(a, s);
-    case 3: return launch_t<1, float>(a, s);
-    case 4: return launch_t<1, __half>(a, s);
-    case 5: return launch_t<1, __nv_bfloat16>(a, s);
-    case 6: return launch_t<2, float>(a, s);
-    case 7: return launch_t<2, __half>(a, s);
-    case 8: return launch_t<2, __nv_bfloat16>(a, s);
+    case 0: return launch_cell<0, float>(a, s);
+    case 1: return launch_cell<0, __half>(a, s);
+    case 2: return launch_cell<0, __nv_bfloat16>(a, s);
+    case 3: return launch_cell<1, float>(a, s);
+    case 4: return launch_cell<1, __half>(a, s);
+    case 5: return launch_cell<1, __nv_bfloat16>(a, s);
+    case 6: return launch_cell<2, float>(a, s);
+    case 7: return launch_cell<2, __half>(a, s);
+    case 8: return launch_cell<2, __nv_bfloat16>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }
