@@ -33,15 +33,65 @@ __device__ __forceinline__ double warp_sum(double v)
 // ------------------------------------------------------------ far field
 // Stage 1: one block per (chunk, angle) sums w J e^{j phi}, w M e^{j phi} over
 // its share of the face cells; writes 12 doubles (Re/Im of N_xyz, L_xyz).
-constexpr int kFFThreads = 256;
+// DFT slot of field component c (0..2) in each mode, or -1 when the mode does
+// not carry it: EZ (E_z, H_x, H_y), HZ (E_x, E_y, H_z), 3D (E_x..E_z, H_x..H_z).
+__host__ __device__ constexpr int slot_E(int mode, int c)
+{
+    return mode == 0 ? (c == 2 ? 0 : -1) : (mode == 1 ? (c < 2 ? c : -1) : c);
+}
+__host__ __device__ constexpr int slot_H(int mode, int c)
+{
+    return mode == 0 ? (c < 2 ? 1 + c : -1) : (mode == 1 ? (c == 2 ? 2 : -1) : 3 + c);
+}
 
+// acc += w e^{j phi} (J, M) of one face cell with outward normal sgn * e_AX,
+// J = n x H, M = -n x E; (e_AX x V)_b1 = -V_b2, (e_AX x V)_b2 = V_b1.
+template <int MODE, int AX>
+__device__ __forceinline__ void face_cell(const double *base, long long plane, double sgn, double wc,
+                                          double ws, double acc[12])
+{
+    constexpr int b1 = (AX + 1) % 3, b2 = (AX + 2) % 3;
+    auto ld = [&](int slot, double &re, double &im) {
+        if (slot < 0) { re = 0.0; im = 0.0; }
+        else { re = base[(2 * slot) * plane]; im = base[(2 * slot + 1) * plane]; }
+    };
+    double Hr1, Hi1, Hr2, Hi2, Er1, Ei1, Er2, Ei2;
+    ld(slot_H(MODE, b1), Hr1, Hi1);
+    ld(slot_H(MODE, b2), Hr2, Hi2);
+    ld(slot_E(MODE, b1), Er1, Ei1);
+    ld(slot_E(MODE, b2), Er2, Ei2);
+    // J_b1 = -sgn H_b2, J_b2 = sgn H_b1, M_b1 = sgn E_b2, M_b2 = -sgn E_b1
+    const double J1r = -sgn * Hr2, J1i = -sgn * Hi2, J2r = sgn * Hr1, J2i = sgn * Hi1;
+    const double M1r = sgn * Er2, M1i = sgn * Ei2, M2r = -sgn * Er1, M2i = -sgn * Ei1;
+    acc[2 * b1 + 0] += J1r * wc - J1i * ws;
+    acc[2 * b1 + 1] += J1r * ws + J1i * wc;
+    acc[2 * b2 + 0] += J2r * wc - J2i * ws;
+    acc[2 * b2 + 1] += J2r * ws + J2i * wc;
+    acc[6 + 2 * b1 + 0] += M1r * wc - M1i * ws;
+    acc[6 + 2 * b1 + 1] += M1r * ws + M1i * wc;
+    acc[6 + 2 * b2 + 0] += M2r * wc - M2i * ws;
+    acc[6 + 2 * b2 + 1] += M2r * ws + M2i * wc;
+}
+
+constexpr int kFFThreads = 256;
+constexpr int kFFTableMax = 4096;   // phase-table entries held in shared memory (64 KB)
+
+// The far-field phase factorises over the coordinates of a face cell,
+//   exp(j k r.(p - c)) = prod_a exp(j k r_a (p_a - c_a)),
+// so with TABLES each block (one angle) first tabulates exp(j k r_a (p_a - c_a))
+// for every coordinate of the NTFF box along the three axes in shared memory,
+// and each (cell, angle) pair then costs two complex products instead of an
+// FP64 sincos.  Without TABLES (very large boxes) the phase is evaluated
+// directly.
+template <int MODE, bool TABLES>
 __global__ void __launch_bounds__(kFFThreads) far_field_partial(const FarFieldArgs a)
 {
+    extern __shared__ double tab[];  // [2 * (n0 + n1 + n2)] (re, im)
     const int ang = blockIdx.y;
     const int chunk = blockIdx.x;
     const double th = a.theta[ang];
     double rh[3];
-    if (a.mode == 2) {
+    if (MODE == 2) {
         const double ph = a.phi[ang];
         rh[0] = sin(th) * cos(ph);
         rh[1] = sin(th) * sin(ph);
@@ -51,8 +101,23 @@ __global__ void __launch_bounds__(kFFThreads) far_field_partial(const FarFieldAr
         rh[1] = sin(th);
         rh[2] = 0.0;
     }
-    const int NE = a.mode == 0 ? 1 : (a.mode == 1 ? 2 : 3);
-    const int NC = a.mode == 2 ? 6 : 3;
+    int toff[3];
+    if (TABLES) {
+        const int n0 = a.g.hi[0] - a.g.lo[0] + 1, n1 = a.g.hi[1] - a.g.lo[1] + 1,
+                  n2 = a.g.hi[2] - a.g.lo[2] + 1;
+        toff[0] = 0;
+        toff[1] = n0;
+        toff[2] = n0 + n1;
+        for (int e = threadIdx.x; e < n0 + n1 + n2; e += blockDim.x) {
+            const int ax = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+            const double pos = a.g.lo[ax] + (e - toff[ax]);
+            double sp, cp;
+            sincos(a.k * rh[ax] * (pos - a.center[ax]), &sp, &cp);
+            tab[2 * e] = cp;
+            tab[2 * e + 1] = sp;
+        }
+        __syncthreads();
+    }
     const long long total = a.g.cell_start[a.g.nfaces];
     const long long per = (total + a.chunks - 1) / a.chunks;
     const long long j0 = (long long)chunk * per;
@@ -70,50 +135,36 @@ __global__ void __launch_bounds__(kFFThreads) far_field_partial(const FarFieldAr
         const int iu = (int)(jl / nv), iv = (int)(jl % nv);
         const int ax = a.g.axis[f];
         const int ua = ax == 2 ? 1 : 2, va = ax == 0 ? 1 : 0;
-        double pos[3];
-        pos[ax] = a.g.side[f] ? a.g.hi[ax] : a.g.lo[ax];
-        pos[ua] = a.g.lo[ua] + iu;
-        pos[va] = a.g.lo[va] + iv;
         // trapezoidal weights: 1/2 on the edges of each face
         double w = 1.0;
         if (nu > 1 && (iu == 0 || iu == nu - 1)) w *= 0.5;
         if (nv > 1 && (iv == 0 || iv == nv - 1)) w *= 0.5;
-        const double phase = a.k * (rh[0] * (pos[0] - a.center[0]) + rh[1] * (pos[1] - a.center[1]) +
-                                    rh[2] * (pos[2] - a.center[2]));
-        double sp, cp;
-        sincos(phase, &sp, &cp);
-        // field phasors of this face cell
+        double cp, sp;
+        if (TABLES) {
+            const int iw = a.g.side[f] ? a.g.hi[ax] - a.g.lo[ax] : 0;
+            const double *tw = tab + 2 * (toff[ax] + iw);
+            const double *tu = tab + 2 * (toff[ua] + iu);
+            const double *tv = tab + 2 * (toff[va] + iv);
+            const double pr = tu[0] * tv[0] - tu[1] * tv[1];
+            const double pi = tu[0] * tv[1] + tu[1] * tv[0];
+            cp = pr * tw[0] - pi * tw[1];
+            sp = pr * tw[1] + pi * tw[0];
+        } else {
+            double pos[3];
+            pos[ax] = a.g.side[f] ? a.g.hi[ax] : a.g.lo[ax];
+            pos[ua] = a.g.lo[ua] + iu;
+            pos[va] = a.g.lo[va] + iv;
+            const double phase = a.k * (rh[0] * (pos[0] - a.center[0]) + rh[1] * (pos[1] - a.center[1]) +
+                                        rh[2] * (pos[2] - a.center[2]));
+            sincos(phase, &sp, &cp);
+        }
         const double *base = a.dft + a.g.off[f] + jl;
         const long long plane = (long long)nu * nv;
-        double Er[3] = {0, 0, 0}, Ei[3] = {0, 0, 0}, Hr[3] = {0, 0, 0}, Hi[3] = {0, 0, 0};
-        for (int k = 0; k < NC; ++k) {
-            const double re = base[(2 * k) * plane], im = base[(2 * k + 1) * plane];
-            int comp;
-            bool isE;
-            if (a.mode == 0) { isE = k < 1; comp = isE ? 2 : k - 1; }
-            else if (a.mode == 1) { isE = k < 2; comp = isE ? k : 2; }
-            else { isE = k < NE; comp = isE ? k : k - 3; }
-            if (isE) { Er[comp] = re; Ei[comp] = im; }
-            else { Hr[comp] = re; Hi[comp] = im; }
-        }
-        // n = side ? +e_ax : -e_ax;  J = n x H, M = -n x E
         const double sgn = a.g.side[f] ? 1.0 : -1.0;
-        double Jr[3], Ji[3], Mr[3], Mi[3];
-        const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
-        // (e_ax x V)_b1 = -V_b2, (e_ax x V)_b2 = V_b1, (e_ax x V)_ax = 0
-        Jr[ax] = 0; Ji[ax] = 0; Mr[ax] = 0; Mi[ax] = 0;
-        Jr[b1] = -sgn * Hr[b2]; Ji[b1] = -sgn * Hi[b2];
-        Jr[b2] = sgn * Hr[b1];  Ji[b2] = sgn * Hi[b1];
-        Mr[b1] = sgn * Er[b2];  Mi[b1] = sgn * Ei[b2];
-        Mr[b2] = -sgn * Er[b1]; Mi[b2] = -sgn * Ei[b1];
         const double wc = w * cp, ws = w * sp;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            acc[2 * c + 0] += Jr[c] * wc - Ji[c] * ws;
-            acc[2 * c + 1] += Jr[c] * ws + Ji[c] * wc;
-            acc[6 + 2 * c + 0] += Mr[c] * wc - Mi[c] * ws;
-            acc[6 + 2 * c + 1] += Mr[c] * ws + Mi[c] * wc;
-        }
+        if (ax == 0) face_cell<MODE, 0>(base, plane, sgn, wc, ws, acc);
+        else if (ax == 1) face_cell<MODE, 1>(base, plane, sgn, wc, ws, acc);
+        else face_cell<MODE, 2>(base, plane, sgn, wc, ws, acc);
     }
 
     __shared__ double red[kFFThreads / 32][12];
@@ -350,10 +401,32 @@ inline int grid_for(long long n, int threads)
 
 }  // namespace
 
+#define LBEM_FF_TABLES(MODE)                                                                 \
+    do {                                                                                     \
+        if (smem > 48 * 1024) {                                                              \
+            cudaError_t e_ = cudaFuncSetAttribute(far_field_partial<MODE, true>,             \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                  kFFTableMax * 2 * (int)sizeof(double));    \
+            if (e_ != cudaSuccess) return e_;                                                \
+        }                                                                                    \
+        far_field_partial<MODE, true><<<g1, kFFThreads, smem, s>>>(a);                       \
+    } while (0)
+
 cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launches)
 {
     dim3 g1(a.chunks, a.n_ang);
-    far_field_partial<<<g1, kFFThreads, 0, s>>>(a);
+    const int entries = (a.g.hi[0] - a.g.lo[0] + 1) + (a.g.hi[1] - a.g.lo[1] + 1) + (a.g.hi[2] - a.g.lo[2] + 1);
+    const bool tables = entries <= kFFTableMax;
+    const size_t smem = tables ? (size_t)entries * 2 * sizeof(double) : 0;
+    switch (a.mode * 2 + (tables ? 1 : 0)) {
+    case 0: far_field_partial<0, false><<<g1, kFFThreads, 0, s>>>(a); break;
+    case 1: LBEM_FF_TABLES(0); break;
+    case 2: far_field_partial<1, false><<<g1, kFFThreads, 0, s>>>(a); break;
+    case 3: LBEM_FF_TABLES(1); break;
+    case 4: far_field_partial<2, false><<<g1, kFFThreads, 0, s>>>(a); break;
+    case 5: LBEM_FF_TABLES(2); break;
+    default: return cudaErrorInvalidValue;
+    }
     far_field_finalize<<<(a.n_ang + 127) / 128, 128, 0, s>>>(a);
     if (launches) *launches += 2;
     return cudaGetLastError();
