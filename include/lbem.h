@@ -210,6 +210,39 @@ int32_t lbem_load_state(lbem_handle h, const void *buf_host, size_t bytes);
 int32_t lbem_set_storage_scale(lbem_handle h, float scale);
 int32_t lbem_get_storage_scale(lbem_handle h, float *scale_out);
 
+/* Far-field projection that allocates nothing (the paper has no counterpart;
+ * this is a library convenience).  For callers that cannot call cudaMalloc or
+ * any allocator -- e.g. a host application that owns the device memory budget
+ * and gives plugins fixed buffers, or a real-time loop where allocation is not
+ * allowed -- it computes the same |S|^2 as lbem_far_field from caller-owned
+ * device memory only:
+ *   dft_dev   the face phasors in the layout of lbem_get_dft (device copy),
+ *   theta_dev, phi_dev (phi ignored, may be NULL, in 2D), n angles,
+ *   s2_dev    n outputs; amp_dev optional (NULL), 12 doubles per angle,
+ * with |E_I| given in desc (e.g. from lbem_incident_amplitude).  Its only
+ * scratch, the partial sums of the projection, lives in a fixed array of
+ * LBEM_NOALLOC_MAX_ANGLES x 16 x 12 doubles (1.5 MB) that every GPU loading
+ * the library holds until the process exits; n > LBEM_NOALLOC_MAX_ANGLES is
+ * rejected with LBEM_ERR_ARG (split larger angle sets over several calls).
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  All calls share the array, so calls whose work overlaps on the GPU
+ * (different streams, or threads) race and must be serialised by the caller.
+ * Asynchronous on cuda_stream (NULL: legacy default stream); errors are
+ * reported by the return code and lbem_last_error(NULL). */
+#define LBEM_NOALLOC_MAX_ANGLES 1024
+typedef struct {
+    int32_t mode;                  /* lbem_mode */
+    int32_t nx, ny, nz;            /* grid extents (nz == 1 for the 2D modes) */
+    int32_t ntff_lo[3], ntff_hi[3];/* NTFF box of the DFT data */
+    double wavelength;             /* cells; k = 2 pi / wavelength */
+    double center[3];              /* phase reference */
+    double incident_amplitude;     /* |E_I| of Eqs. 5-6 */
+} lbem_ntff_desc;
+int32_t lbem_far_field_noalloc(const lbem_ntff_desc *desc, const double *dft_dev,
+                               const double *theta_dev, const double *phi_dev, int32_t n,
+                               double *s2_dev, double *amp_dev, void *cuda_stream);
+
 /* Wait for the handle's stream; reports an asynchronous CUDA error. */
 int32_t lbem_sync(lbem_handle h);
 

@@ -56,6 +56,11 @@ struct lbem_ctx {
 
 static thread_local char g_create_err[512] = "";
 
+namespace lbem {
+// Message of a failed call that has no handle (read by lbem_last_error(NULL)).
+void set_noctx_error(const char *msg) { snprintf(g_create_err, sizeof g_create_err, "%s", msg); }
+}
+
 static int fail(lbem_ctx *h, int code, const char *fmt, ...)
 {
     char *buf = h ? h->err : g_create_err;

@@ -133,6 +133,7 @@ struct FarFieldArgs {
     double *amp;               // [n_ang][12]
 };
 cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launches);
+cudaError_t launch_far_field_partial(const FarFieldArgs &a, cudaStream_t s);
 
 cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int nz, int nxp,
                            int *bad_flag, cudaStream_t s);

@@ -432,6 +432,25 @@ cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launche
     return cudaGetLastError();
 }
 
+// The projection's partial-sum stage alone (the caller finalises).
+cudaError_t launch_far_field_partial(const FarFieldArgs &a, cudaStream_t s)
+{
+    dim3 g1(a.chunks, a.n_ang);
+    const int entries = (a.g.hi[0] - a.g.lo[0] + 1) + (a.g.hi[1] - a.g.lo[1] + 1) + (a.g.hi[2] - a.g.lo[2] + 1);
+    const bool tables = entries <= kFFTableMax;
+    const size_t smem = tables ? (size_t)entries * 2 * sizeof(double) : 0;
+    switch (a.mode * 2 + (tables ? 1 : 0)) {
+    case 0: far_field_partial<0, false><<<g1, kFFThreads, 0, s>>>(a); break;
+    case 1: LBEM_FF_TABLES(0); break;
+    case 2: far_field_partial<1, false><<<g1, kFFThreads, 0, s>>>(a); break;
+    case 3: LBEM_FF_TABLES(1); break;
+    case 4: far_field_partial<2, false><<<g1, kFFThreads, 0, s>>>(a); break;
+    case 5: LBEM_FF_TABLES(2); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int nz, int nxp,
                            int *bad_flag, cudaStream_t s)
 {

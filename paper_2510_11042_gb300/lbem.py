@@ -50,6 +50,15 @@ class PlaneWaveDesc(ctypes.Structure):
                 ("center", ctypes.c_double * 3), ("source_index", ctypes.c_int32)]
 
 
+class NtffDesc(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("ntff_lo", ctypes.c_int32 * 3),
+                ("ntff_hi", ctypes.c_int32 * 3), ("wavelength", ctypes.c_double),
+                ("center", ctypes.c_double * 3), ("incident_amplitude", ctypes.c_double)]
+
+
+LBEM_NOALLOC_MAX_ANGLES = 1024
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
@@ -75,6 +84,7 @@ _SIGS = {
     "lbem_load_state": (_I32, [_P, _P, ctypes.c_size_t]),
     "lbem_set_storage_scale": (_I32, [_P, ctypes.c_float]),
     "lbem_get_storage_scale": (_I32, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "lbem_far_field_noalloc": (_I32, [ctypes.POINTER(NtffDesc), _P, _P, _P, _I32, _P, _P, _P]),
     "lbem_sync": (_I32, [_P]),
     "lbem_destroy": (None, [_P]),
     "lbem_last_error": (ctypes.c_char_p, [_P]),
@@ -267,6 +277,18 @@ def lbem_get_storage_scale(h) -> float:
     v = ctypes.c_float()
     _check(lib().lbem_get_storage_scale(h, ctypes.byref(v)), h)
     return v.value
+
+
+def lbem_far_field_noalloc(desc: NtffDesc, dft_dev, theta_dev, phi_dev, s2_dev, amp_dev=None,
+                           stream=None):
+    """Device tensors in and out (torch CUDA tensors); allocates nothing."""
+    dp, _ = _ptr(dft_dev)
+    tp, _ = _ptr(theta_dev)
+    pp, _ = _ptr(phi_dev)
+    sp, _ = _ptr(s2_dev)
+    ap, _ = _ptr(amp_dev)
+    n = theta_dev.numel() if hasattr(theta_dev, "numel") else len(theta_dev)
+    _check(lib().lbem_far_field_noalloc(ctypes.byref(desc), dp, tp, pp, int(n), sp, ap, stream))
 
 
 def lbem_sync(h):
