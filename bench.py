@@ -253,6 +253,7 @@ def run_gpu(args, rank, world, local_rank):
 
     K, Wm = args.steps, args.warmup
     main = one_storage("f32", K, Wm, True)
+    batched = None if (args.no_batch or world > 1) else run_batched(dev)
     secondary = {}
     if not args.fp32_only:
         for st in ("f16", "bf16"):
@@ -317,9 +318,92 @@ def run_gpu(args, rank, world, local_rank):
                 "periods_run": main["periods"], "incident_amplitude": round(main["incident"], 6)},
         "storage_modes": storage_modes,
     }
+    if batched:
+        line["batched"] = batched
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.size, budget_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ batched workload
+def small_problems(count=64, seed=7):
+    """Launch-bound batch: cylinders of N = 64..192 (multiples of 32), W = 8,
+    eps_r in [1.5, 6], x in [1, 3], lambda = 8..16 cells, 300 steps each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        n = 32 * int(rng.integers(2, 7))
+        lam = float(rng.integers(8, 17))
+        x = float(rng.uniform(1.0, 3.0))
+        eps_in = float(rng.uniform(1.5, 6.0))
+        a = x * lam / (2 * math.pi)
+        if 2 * a + 2 * (8 + 6) > n:
+            continue
+        p = W.cylinder_problem(n=n, x=x, wavelength=lam, eps_in=eps_in, w=8, mode="ez", periods=1,
+                               gap_ntff=2, gap_tf=2)
+        out.append(W.with_steps(p, 300))
+    return out
+
+
+def run_batched(dev, count=32, seed=20251011):
+    """32 seeded cylinders (N = 256..1024, eps_r in [1.5, 6], x in [1, 10],
+    lambda = 24..48 cells, W = 16, 40 periods each) in one persistent batched
+    run (autotuned launch shape) and, for comparison, stepped one problem after
+    another with one launch per step.  Aggregate MLUPS = sum(cells x steps) / s."""
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    out = {}
+    for label, probs in (("cylinders_256_1024", W.batched_problems(count, seed)),
+                         ("small_64_192", small_problems())):
+        out[label] = _batch_vs_sequential(dev, probs)
+    out["cylinders_256_1024"]["workload"] = (f"{count} cylinders, seed {seed}, N 256-1024, "
+                                             "40 periods each, FP32, EZ")
+    out["small_64_192"]["workload"] = "64 cylinders, seed 7, N 64-192, 300 steps each, FP32, EZ"
+    return out
+
+
+def _batch_vs_sequential(dev, probs):
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    work = sum(p.shape[0] * p.shape[1] * p.steps for p in probs)
+
+    def solvers():
+        out = []
+        for p in probs:
+            s = lbem.Solver(p.shape, p.eps, p.mode, "f32", p.absorber_width, p.sigma_max, device=dev)
+            s.inject(p.wave)
+            s.set_dft_window(p.dft_start, p.dft_periods)
+            out.append(s)
+        torch.cuda.synchronize(dev)
+        return out
+
+    sol = solvers()
+    batch = lbem.Batch(sol)
+    t0 = time.perf_counter()
+    batch.run([p.steps for p in probs], autotune=True)
+    torch.cuda.synchronize(dev)
+    t_batch = time.perf_counter() - t0
+    bps, rpi, _ = batch.config()
+    batch.close()
+    for s in sol:
+        s.close()
+    del sol
+    torch.cuda.empty_cache()
+
+    sol = solvers()
+    t0 = time.perf_counter()
+    for s, p in zip(sol, probs):
+        s.step(p.steps)
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    for s in sol:
+        s.close()
+    del sol
+    torch.cuda.empty_cache()
+    return {"cell_updates": work, "persistent_mlups": round(work / t_batch / 1e6, 1),
+            "sequential_mlups": round(work / t_seq / 1e6, 1),
+            "speedup": round(t_seq / t_batch, 3),
+            "autotuned": {"blocks_per_sm": bps, "rows_per_item": rpi}}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -414,6 +498,7 @@ def main():
     ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
     ap.add_argument("--size", type=int, default=384)
     ap.add_argument("--fp32-only", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-updates", type=float, default=2)

@@ -210,6 +210,29 @@ int32_t lbem_load_state(lbem_handle h, const void *buf_host, size_t bytes);
 int32_t lbem_set_storage_scale(lbem_handle h, float scale);
 int32_t lbem_get_storage_scale(lbem_handle h, float *scale_out);
 
+/* Batched runs (the workload of many uneven scatterers advanced together):
+ * a batch groups existing handles of the same mode and storage on one device
+ * and advances them in one persistent cooperative launch whose blocks stride
+ * over the row tiles of all problems, with a bounded grid barrier between
+ * steps.  lbem_batch_run(b, steps, autotune) advances handle i by steps[i]
+ * (problems that are done drop out); with autotune the first call times a
+ * few candidate launch shapes (blocks per SM, rows per work item) on its
+ * first steps, which count as real steps (the results do not depend on the
+ * shape), and keeps the fastest.  The handles' own streams are synchronised
+ * first; the batch runs on cuda_stream and returns when it is done.
+ * LBEM_ERR_TIMEOUT reports a grid-barrier wait that ran out.  workspace: as
+ * in lbem_create (NULL: the library allocates it). */
+typedef struct lbem_batch_ctx *lbem_batch;
+int32_t lbem_batch_workspace_bytes(int32_t count, size_t *bytes_out);
+int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, void *cuda_stream,
+                          void *workspace, size_t workspace_bytes, lbem_batch *out);
+int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t autotune);
+int32_t lbem_batch_config(lbem_batch b, int32_t *blocks_per_sm, int32_t *rows_per_item,
+                          double *ms_per_step);
+int64_t lbem_batch_launches(lbem_batch b);
+const char *lbem_batch_last_error(lbem_batch b);
+void lbem_batch_destroy(lbem_batch b);
+
 /* Far-field projection that allocates nothing (the paper has no counterpart;
  * this is a library convenience).  For callers that cannot call cudaMalloc or
  * any allocator -- e.g. a host application that owns the device memory budget

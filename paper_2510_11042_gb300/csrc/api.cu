@@ -513,6 +513,249 @@ int32_t lbem_step(lbem_handle h, int64_t n)
     return LBEM_OK;
 }
 
+// ------------------------------------------------------------ batched runs
+struct lbem_batch_ctx {
+    std::vector<lbem_ctx *> hs;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    bool owns_ws = false;
+    BatchProblem *table = nullptr;   // device
+    unsigned *bar = nullptr;         // device: count, generation
+    int *status = nullptr;           // device
+    int mode = 0, storage = 0;
+    int tuned = 0, best_bps = 0, best_rpi = 1;
+    double best_ms = 0.0;
+    int64_t launches = 0;
+    char err[512];
+};
+
+static int bfail(lbem_batch_ctx *b, int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b ? b->err : g_create_err, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static size_t batch_bytes(int count)
+{
+    return align256((size_t)count * sizeof(BatchProblem)) + 256;
+}
+
+extern "C" int32_t lbem_batch_workspace_bytes(int32_t count, size_t *bytes_out)
+{
+    if (count < 1 || !bytes_out) return bfail(nullptr, LBEM_ERR_ARG, "need count >= 1 and bytes_out");
+    *bytes_out = batch_bytes(count);
+    return LBEM_OK;
+}
+
+extern "C" int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, void *cuda_stream,
+                                     void *workspace, size_t workspace_bytes, lbem_batch *out)
+{
+    if (!out) return bfail(nullptr, LBEM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!handles || count < 1) return bfail(nullptr, LBEM_ERR_ARG, "need at least one handle");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < count; ++i) {
+        if (!handles[i]) return bfail(nullptr, LBEM_ERR_ARG, "handle %d is NULL", i);
+        if (handles[i]->g.mode != handles[0]->g.mode || handles[i]->g.storage != handles[0]->g.storage)
+            return bfail(nullptr, LBEM_ERR_ARG, "all handles of a batch need the same mode and storage");
+        if (handles[i]->device != dev) return bfail(nullptr, LBEM_ERR_ARG, "handle %d is on another device", i);
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return bfail(nullptr, LBEM_ERR_ARG, "handle %d repeated", i);
+    }
+    const size_t need = batch_bytes(count);
+    if (workspace && ((uintptr_t)workspace & 255)) return bfail(nullptr, LBEM_ERR_ARG, "workspace must be 256-byte aligned");
+    if (workspace && workspace_bytes < need)
+        return bfail(nullptr, LBEM_ERR_OOM, "batch workspace of %zu bytes < %zu", workspace_bytes, need);
+    lbem_batch_ctx *b = new (std::nothrow) lbem_batch_ctx();
+    if (!b) return bfail(nullptr, LBEM_ERR_OOM, "host allocation failed");
+    b->hs.assign(handles, handles + count);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->mode = handles[0]->g.mode;
+    b->storage = handles[0]->g.storage;
+    if (workspace) {
+        b->ws = (char *)workspace;
+    } else {
+        if (cudaMalloc((void **)&b->ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return bfail(nullptr, LBEM_ERR_OOM, "cudaMalloc of the batch workspace failed");
+        }
+        b->owns_ws = true;
+    }
+    b->table = (BatchProblem *)b->ws;
+    b->bar = (unsigned *)(b->ws + align256((size_t)count * sizeof(BatchProblem)));
+    b->status = (int *)(b->bar + 2);
+    b->err[0] = 0;
+    *out = b;
+    return LBEM_OK;
+}
+
+// Run every problem of the batch min(left_i, chunk) steps in one cooperative launch.
+static int batch_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t chunk, int bps, int rpi,
+                       cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    const int n = (int)b->hs.size();
+    std::vector<BatchProblem> tab(n);
+    int items = 0;
+    int64_t max_steps = 0;
+    for (int i = 0; i < n; ++i) {
+        lbem_ctx *h = b->hs[i];
+        BatchProblem &P = tab[i];
+        std::memset(&P, 0, sizeof P);
+        fill_common_args(h, P.a);
+        P.a.nblk_x = (h->g.nx + 127) / 128;
+        const int rows = h->g.ny * h->g.nz;
+        P.nitems = P.a.nblk_x * ((rows + rpi - 1) / rpi);
+        P.a.nblk_main = P.nitems;
+        if (h->has_wave && (h->n_line + 127) / 128 > P.nitems)
+            return bfail(b, LBEM_ERR_ARG, "problem %d is too small for %d rows per work item", i, rpi);
+        P.item0 = items;
+        items += P.nitems;
+        P.f_base[0] = (const char *)h->f[0];
+        P.f_base[1] = (const char *)h->f[1];
+        for (int k = 0; k < 3; ++k) P.line[k] = h->line[k];
+        P.plane_bytes = (long long)h->P * (long long)h->elem;
+        P.t0 = h->t;
+        P.steps = std::min<int64_t>(left[i], chunk);
+        P.cur0 = h->cur;
+        P.scale = h->scale;
+        P.has_wave = h->has_wave ? 1 : 0;
+        if (h->has_wave) {
+            P.T = h->T;
+            P.amp = h->wave.amplitude;
+            P.t_ramp = h->wave.ramp_periods * h->T;
+            const double *d = h->wave.dir, *p = h->wave.pol;
+            const double kxp[3] = {d[1] * p[2] - d[2] * p[1], d[2] * p[0] - d[0] * p[2], d[0] * p[1] - d[1] * p[0]};
+            for (int c = 0; c < 3; ++c) {
+                P.pol[c] = (float)p[c];
+                P.kxp[c] = (float)kxp[c];
+            }
+            P.dft_t0 = h->dft_t0;
+            P.dft_periods = h->dft_periods;
+        } else {
+            P.T = 1;
+        }
+        max_steps = std::max<int64_t>(max_steps, P.steps);
+    }
+    if (max_steps == 0) return LBEM_OK;
+    if (cudaMemcpyAsync(b->table, tab.data(), n * sizeof(BatchProblem), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned) + sizeof(int), b->stream) != cudaSuccess)
+        return bfail(b, LBEM_ERR_CUDA, "batch table upload failed");
+    BatchArgs a;
+    a.probs = b->table;
+    a.nprob = n;
+    a.nitems = items;
+    a.rows_per_item = rpi;
+    a.max_steps = max_steps;
+    a.bar_count = b->bar;
+    a.bar_gen = b->bar + 1;
+    a.status = b->status;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->hs[0]->device);
+    const int grid = std::max(1, std::min(bps * sms, items));
+    if (ev0) cudaEventRecord(ev0, b->stream);
+    cudaError_t e = launch_batch(b->mode, b->storage, a, grid, b->stream);
+    if (ev1) cudaEventRecord(ev1, b->stream);
+    if (e != cudaSuccess) return bfail(b, LBEM_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+    b->launches += 1;
+    for (int i = 0; i < n; ++i) {
+        lbem_ctx *h = b->hs[i];
+        const int64_t k = tab[i].steps;
+        h->t += k;
+        h->cur ^= (int)(k & 1);
+        left[i] -= k;
+    }
+    int st = 0;
+    if (cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return bfail(b, LBEM_ERR_CUDA, "batch run: %s", cudaGetErrorString(cudaGetLastError()));
+    if (st & 2) return bfail(b, LBEM_ERR_TIMEOUT, "a grid-barrier wait of the batched kernel ran out");
+    return LBEM_OK;
+}
+
+extern "C" int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t autotune)
+{
+    if (!b) return bfail(nullptr, LBEM_ERR_ARG, "NULL batch");
+    if (!steps) return bfail(b, LBEM_ERR_ARG, "steps is NULL");
+    const int n = (int)b->hs.size();
+    std::vector<int64_t> left(steps, steps + n);
+    for (int i = 0; i < n; ++i)
+        if (left[i] < 0) return bfail(b, LBEM_ERR_ARG, "steps[%d] < 0", i);
+    for (lbem_ctx *h : b->hs)
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bfail(b, LBEM_ERR_CUDA, "handle stream failed");
+    const int max_bps = batch_max_blocks_per_sm(b->mode, b->storage);
+    if (max_bps < 1) return bfail(b, LBEM_ERR_CUDA, "the batched kernel cannot be resident");
+    if (autotune && !b->tuned) {
+        // time a few steps of each candidate; steps taken while tuning count
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const int64_t trial = 8;
+        double best = 1e300;
+        const int bps_c[4] = {1, 2, max_bps / 2, max_bps};
+        const int rpi_c[3] = {1, 2, 4};
+        for (int ib = 0; ib < 4; ++ib) {
+            const int bps = std::max(1, std::min(max_bps, bps_c[ib]));
+            for (int ir = 0; ir < 3; ++ir) {
+                int64_t active = 0;
+                for (int64_t v : left) active = std::max(active, std::min<int64_t>(v, trial));
+                if (active < trial) break;
+                int rc = batch_chunk(b, left, trial, bps, rpi_c[ir], e0, e1);
+                if (rc != LBEM_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return rc;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / trial < best) {
+                    best = ms / trial;
+                    b->best_bps = bps;
+                    b->best_rpi = rpi_c[ir];
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (b->best_bps > 0) {
+            b->tuned = 1;
+            b->best_ms = best;
+        }
+    }
+    const int bps = b->best_bps > 0 ? b->best_bps : max_bps;
+    int64_t remaining = 0;
+    for (int64_t v : left) remaining = std::max(remaining, v);
+    return batch_chunk(b, left, remaining, bps, b->best_rpi, nullptr, nullptr);
+}
+
+extern "C" int32_t lbem_batch_config(lbem_batch b, int32_t *blocks_per_sm, int32_t *rows_per_item,
+                                     double *ms_per_step)
+{
+    if (!b) return bfail(nullptr, LBEM_ERR_ARG, "NULL batch");
+    if (blocks_per_sm) *blocks_per_sm = b->best_bps;
+    if (rows_per_item) *rows_per_item = b->best_rpi;
+    if (ms_per_step) *ms_per_step = b->best_ms;
+    return LBEM_OK;
+}
+
+extern "C" int64_t lbem_batch_launches(lbem_batch b) { return b ? b->launches : 0; }
+
+extern "C" const char *lbem_batch_last_error(lbem_batch b) { return b ? b->err : g_create_err; }
+
+extern "C" void lbem_batch_destroy(lbem_batch b)
+{
+    if (!b) return;
+    if (b->owns_ws) {
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->ws);
+    }
+    delete b;
+}
+
 int32_t lbem_get_time(lbem_handle h, int64_t *t_out)
 {
     if (!h || !t_out) return fail(h, LBEM_ERR_ARG, "NULL argument");

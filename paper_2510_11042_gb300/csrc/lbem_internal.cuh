@@ -92,7 +92,39 @@ struct StepArgs {
     float scale, inv_scale;
 };
 
+// One problem of a batched run (device copy; see lbem_batch_run).
+struct BatchProblem {
+    StepArgs a;                 // static arguments; per-step fields filled in the kernel
+    const char *f_base[2];      // the two population buffers
+    float *line[3];             // incident line buffers, line(t) in line[t % 3]
+    long long plane_bytes;
+    long long t0, steps;        // time at the start of the run, steps to take
+    int cur0;                   // buffer holding f*(t0)
+    int T;                      // period in steps
+    int nitems;                 // work items (row tiles) of this problem
+    int item0;                  // first work item in the batch's list
+    int has_wave;
+    double amp, t_ramp;         // incident amplitude and ramp length (steps)
+    float pol[3], kxp[3];       // p_hat and k_hat x p_hat
+    long long dft_t0;           // first field time of the DFT window (< 1: none)
+    int dft_periods;
+    double scale;               // storage scale
+};
+
+struct BatchArgs {
+    const BatchProblem *probs;
+    int nprob;
+    int nitems;
+    int rows_per_item;          // rows of 128-cell tiles per work item
+    long long max_steps;
+    unsigned *bar_count;        // grid barrier: arrivals and generation
+    unsigned *bar_gen;
+    int *status;                // bit 1: a grid-barrier wait ran out
+};
+
 // Launchers (step.cu)
+cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cudaStream_t s);
+int batch_max_blocks_per_sm(int mode, int storage);
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_line_init(int mode, const StepArgs &a, cudaStream_t s);
 

@@ -338,18 +338,12 @@ template <> __device__ __forceinline__ void store_pop<__nv_bfloat16>(__nv_bfloat
 // 32-bit in-plane offset from a constant-bank base; the +-x pulls are plain
 // loads shifted by one element (coalesced; the extra sector per warp hits in
 // L1/L2).
+// The cells x = bx * BX + threadIdx.x of row (y, z) for one step.
 template <int MODE, class S, int BX>
-__global__ void __launch_bounds__(BX, sizeof(S) == 4 ? 6 : 7) step_kernel_cell(const StepArgs a)
+__device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int z)
 {
     using PL = Planes<MODE>;
     constexpr int Q = PL::Q;
-    const int b = blockIdx.x;
-    if (a.line_on) {
-        const int s = b * BX + threadIdx.x;
-        if (s < a.n_line) line_work<MODE>(a, s);
-    }
-    int bx, y, z;
-    block_row(a, b, bx, y, z);
     const int x = bx * BX + threadIdx.x;
     if (x >= a.nx) return;
 
@@ -373,6 +367,152 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 4 ? 6 : 7) step_kernel_cell(c
     for (int q = 0; q < Q; ++q) store_pop<S>(static_cast<S *>(a.fout_q[q]) + c, f[q]);
 }
 
+template <int MODE, class S, int BX>
+__global__ void __launch_bounds__(BX, sizeof(S) == 4 ? 6 : 7) step_kernel_cell(const StepArgs a)
+{
+    const int b = blockIdx.x;
+    if (a.line_on) {
+        const int s = b * BX + threadIdx.x;
+        if (s < a.n_line) line_work<MODE>(a, s);
+    }
+    int bx, y, z;
+    block_row(a, b, bx, y, z);
+    row_cells<MODE, S, BX>(a, bx, y, z);
+}
+
+constexpr int kBX = 128;  // threads per block = cells per row tile
+
+// ---------------------------------------------------------------------------
+// Batched persistent kernel: many problems (same mode and storage, any sizes,
+// wavelengths and step counts) advance together in one cooperative launch.
+// Each global step, the resident blocks stride over a flat list of work items
+// (tiles of kBX cells x rows_per_item rows of one problem); a block copies its
+// problem's arguments to shared memory and fills in the per-step ones (buffer
+// parity, incident-line buffers, hard-source fields at t+2, DFT phase at t+1)
+// before running the same row update as the single-problem kernel.  Problems
+// that have taken their steps drop out.  Steps are separated by a grid
+// barrier whose wait is bounded: a block that gives up sets status bit 1 and
+// the kernel stops.
+constexpr long long kBarrierPolls = 1LL << 22;   // ~1 s of 256 ns sleeps
+
+__device__ bool grid_barrier(const BatchArgs &b, unsigned nblocks)
+{
+    __shared__ int give_up;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        give_up = 0;
+        volatile unsigned *gen = b.bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(b.bar_count, 1u) == nblocks - 1) {
+            *b.bar_count = 0;
+            __threadfence();
+            atomicAdd(b.bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > kBarrierPolls) {
+                    atomicOr(b.status, 2);
+                    give_up = 1;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return give_up == 0;
+}
+
+// Per-step arguments of problem P at its time t (state f*(t) -> f*(t+1)).
+__device__ void fill_step_args(StepArgs &sa, const BatchProblem &P, long long step, int Q)
+{
+    const long long t = P.t0 + step;
+    const int in = (P.cur0 + (int)(step & 1)) & 1;
+    for (int q = 0; q < Q; ++q) {
+        sa.fin_q[q] = P.f_base[in] + q * P.plane_bytes;
+        sa.fout_q[q] = (void *)(P.f_base[in ^ 1] + q * P.plane_bytes);
+    }
+    if (!P.has_wave) return;
+    sa.line_n1 = P.line[(t + 1) % 3];
+    sa.line_out = P.line[(t + 2) % 3];
+    // hard source at time t+2: E = E0 ramp(t) sin(w t) p, H = k x E
+    const long long ts = t + 2;
+    const double tr = (double)ts;
+    double ramp = 1.0;
+    if (tr <= 0.0) ramp = 0.0;
+    else if (tr < P.t_ramp) ramp = 0.5 * (1.0 - cospi(tr / P.t_ramp));
+    const double sv = P.amp * ramp * sinpi(2.0 * (double)(ts % P.T) / (double)P.T);
+    for (int c = 0; c < 3; ++c) {
+        sa.src_E[c] = (float)(sv * P.pol[c]);
+        sa.src_H[c] = (float)(sv * P.kxp[c]);
+    }
+    // DFT of the fields at time t+1
+    const long long tf = t + 1;
+    sa.dft_on = (P.dft_t0 >= 1 && tf >= P.dft_t0 && tf < P.dft_t0 + (long long)P.dft_periods * P.T);
+    if (sa.dft_on) {
+        double sp, cp;
+        sincospi(2.0 * (double)(tf % P.T) / (double)P.T, &sp, &cp);
+        sa.dft_c = cp;
+        sa.dft_s = sp;
+        sa.dft_scale = 2.0 / ((double)P.dft_periods * P.T);
+        sa.dft_scale_cells = sa.dft_scale * P.scale;
+    }
+}
+
+template <int MODE, class S>
+__global__ void __launch_bounds__(kBX) batch_kernel(const BatchArgs b)
+{
+    constexpr int Q = Planes<MODE>::Q;
+    __shared__ StepArgs sa;        // arguments of (cached_pi, cached_step)
+    __shared__ int s_pi;
+    int cached_pi = -1;
+    long long cached_step = -1;
+    for (long long step = 0; step < b.max_steps; ++step) {
+        for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
+            if (threadIdx.x == 0) {
+                int lo = 0, hi = b.nprob - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) / 2;
+                    if (b.probs[mid].item0 <= item) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_pi = lo;
+            }
+            __syncthreads();
+            const int pi = s_pi;
+            const BatchProblem &P = b.probs[pi];
+            if (step < P.steps) {  // uniform over the block
+                if (pi != cached_pi || step != cached_step) {
+                    const int *src = reinterpret_cast<const int *>(&P.a);
+                    int *dst = reinterpret_cast<int *>(&sa);
+                    for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / sizeof(int)); i += blockDim.x)
+                        dst[i] = src[i];
+                    __syncthreads();
+                    if (threadIdx.x == 0) fill_step_args(sa, P, step, Q);
+                    __syncthreads();
+                    cached_pi = pi;
+                    cached_step = step;
+                }
+                const int li = item - P.item0;
+                if (sa.line_on) {
+                    const int sl = li * kBX + threadIdx.x;
+                    if (sl < sa.n_line) line_work<MODE>(sa, sl);
+                }
+                const int rows = sa.ny * sa.nz;
+                const int r0 = (li / sa.nblk_x) * b.rows_per_item;
+                const int bx = li % sa.nblk_x;
+                for (int r = r0; r < min(r0 + b.rows_per_item, rows); ++r)
+                    row_cells<MODE, S, kBX>(sa, bx, r % sa.ny, r / sa.ny);
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(b, gridDim.x)) return;
+        if (*((volatile int *)b.status) & 2) return;
+    }
+}
+
 // First update of a freshly started incident line: line(t+1) from line(t).
 template <int MODE>
 __global__ void line_init_kernel(const StepArgs a)
@@ -384,7 +524,6 @@ __global__ void line_init_kernel(const StepArgs a)
                         a.inc_axis);
 }
 
-constexpr int kBX = 128;
 
 template <int MODE, class S>
 cudaError_t launch_cell(StepArgs a, cudaStream_t s)
@@ -396,7 +535,54 @@ cudaError_t launch_cell(StepArgs a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int MODE, class S>
+cudaError_t launch_batch_t(const BatchArgs &b, int grid, cudaStream_t s)
+{
+    void *args[] = {const_cast<BatchArgs *>(&b)};
+    return cudaLaunchCooperativeKernel((const void *)batch_kernel<MODE, S>, dim3(grid), dim3(kBX), args, 0, s);
+}
+
+template <int MODE, class S>
+int max_blocks_t()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<MODE, S>, kBX, 0) != cudaSuccess) return 0;
+    return n;
+}
+
 }  // namespace
+
+cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cudaStream_t s)
+{
+    switch (mode * 3 + storage) {
+    case 0: return launch_batch_t<0, float>(b, grid, s);
+    case 1: return launch_batch_t<0, __half>(b, grid, s);
+    case 2: return launch_batch_t<0, __nv_bfloat16>(b, grid, s);
+    case 3: return launch_batch_t<1, float>(b, grid, s);
+    case 4: return launch_batch_t<1, __half>(b, grid, s);
+    case 5: return launch_batch_t<1, __nv_bfloat16>(b, grid, s);
+    case 6: return launch_batch_t<2, float>(b, grid, s);
+    case 7: return launch_batch_t<2, __half>(b, grid, s);
+    case 8: return launch_batch_t<2, __nv_bfloat16>(b, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int batch_max_blocks_per_sm(int mode, int storage)
+{
+    switch (mode * 3 + storage) {
+    case 0: return max_blocks_t<0, float>();
+    case 1: return max_blocks_t<0, __half>();
+    case 2: return max_blocks_t<0, __nv_bfloat16>();
+    case 3: return max_blocks_t<1, float>();
+    case 4: return max_blocks_t<1, __half>();
+    case 5: return max_blocks_t<1, __nv_bfloat16>();
+    case 6: return max_blocks_t<2, float>();
+    case 7: return max_blocks_t<2, __half>();
+    case 8: return max_blocks_t<2, __nv_bfloat16>();
+    default: return 0;
+    }
+}
 
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s)
 {

@@ -85,6 +85,14 @@ _SIGS = {
     "lbem_set_storage_scale": (_I32, [_P, ctypes.c_float]),
     "lbem_get_storage_scale": (_I32, [_P, ctypes.POINTER(ctypes.c_float)]),
     "lbem_far_field_noalloc": (_I32, [ctypes.POINTER(NtffDesc), _P, _P, _P, _I32, _P, _P, _P]),
+    "lbem_batch_workspace_bytes": (_I32, [_I32, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbem_batch_create": (_I32, [ctypes.POINTER(_P), _I32, _P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "lbem_batch_run": (_I32, [_P, ctypes.POINTER(_I64), _I32]),
+    "lbem_batch_config": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                 ctypes.POINTER(ctypes.c_double)]),
+    "lbem_batch_launches": (_I64, [_P]),
+    "lbem_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbem_batch_destroy": (None, [_P]),
     "lbem_sync": (_I32, [_P]),
     "lbem_destroy": (None, [_P]),
     "lbem_last_error": (ctypes.c_char_p, [_P]),
@@ -289,6 +297,83 @@ def lbem_far_field_noalloc(desc: NtffDesc, dft_dev, theta_dev, phi_dev, s2_dev, 
     ap, _ = _ptr(amp_dev)
     n = theta_dev.numel() if hasattr(theta_dev, "numel") else len(theta_dev)
     _check(lib().lbem_far_field_noalloc(ctypes.byref(desc), dp, tp, pp, int(n), sp, ap, stream))
+
+
+def _bcheck(rc, b=None):
+    if rc != LBEM_OK:
+        msg = lib().lbem_batch_last_error(b)
+        raise LbemError(rc, msg.decode() if msg else "")
+
+
+def lbem_batch_workspace_bytes(count: int) -> int:
+    n = ctypes.c_size_t()
+    _bcheck(lib().lbem_batch_workspace_bytes(int(count), ctypes.byref(n)))
+    return n.value
+
+
+def lbem_batch_create(handles, stream=None, workspace=None) -> int:
+    arr = (_P * len(handles))(*handles)
+    wp, _ = _ptr(workspace)
+    wb = workspace.numel() if workspace is not None else 0
+    b = _P()
+    _bcheck(lib().lbem_batch_create(arr, len(handles), stream, wp, wb, ctypes.byref(b)))
+    return b.value
+
+
+def lbem_batch_run(b, steps, autotune=True):
+    arr = (_I64 * len(steps))(*[int(v) for v in steps])
+    _bcheck(lib().lbem_batch_run(b, arr, 1 if autotune else 0), b)
+
+
+def lbem_batch_config(b):
+    bps, rpi, ms = _I32(), _I32(), ctypes.c_double()
+    _bcheck(lib().lbem_batch_config(b, ctypes.byref(bps), ctypes.byref(rpi), ctypes.byref(ms)), b)
+    return bps.value, rpi.value, ms.value
+
+
+def lbem_batch_launches(b) -> int:
+    return int(lib().lbem_batch_launches(b))
+
+
+def lbem_batch_last_error(b=None) -> str:
+    m = lib().lbem_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def lbem_batch_destroy(b):
+    lib().lbem_batch_destroy(b)
+
+
+class Batch:
+    """Several Solvers advanced together in one persistent launch."""
+
+    def __init__(self, solvers):
+        import torch
+        self.solvers = list(solvers)
+        dev = self.solvers[0].device
+        with torch.cuda.device(dev):
+            self.workspace = torch.empty(lbem_batch_workspace_bytes(len(self.solvers)),
+                                         dtype=torch.uint8, device=dev)
+            self.stream = torch.cuda.current_stream(dev)
+            self.b = lbem_batch_create([s.h for s in self.solvers], self.stream.cuda_stream,
+                                       self.workspace)
+
+    def run(self, steps, autotune=True):
+        lbem_batch_run(self.b, steps, autotune)
+
+    def config(self):
+        return lbem_batch_config(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbem_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lbem_sync(h):

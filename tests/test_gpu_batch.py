@@ -1,0 +1,56 @@
+"""Batched persistent launch: uneven problems advanced together must give the
+same state, DFT and far field as each problem stepped on its own (which the
+parity tests compare with the FP64 oracle)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from _parity import angles, gpu_solver, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def problems():
+    return [W.cylinder_problem(n=96, x=2.0, wavelength=8.0, eps_in=3.0, w=8, mode="ez", periods=14),
+            W.cylinder_problem(n=160, x=5.0, wavelength=16.0, eps_in=2.25, w=12, mode="ez", periods=6),
+            W.cylinder_problem(n=128, x=3.0, wavelength=12.0, eps_in=5.0, w=10, mode="ez", periods=8)]
+
+
+def test_batch_matches_single_runs():
+    from paper_2510_11042_gb300 import lbem
+    probs = problems()
+    singles = [gpu_solver(p) for p in probs]
+    batched = [gpu_solver(p, steps=0) for p in probs]
+    batch = lbem.Batch(batched)
+    batch.run([p.steps for p in probs], autotune=True)
+    bps, rpi, ms = batch.config()
+    assert bps >= 1 and rpi in (1, 2, 4) and ms > 0
+    th, _ = angles("ez")
+    for p, s1, s2 in zip(probs, singles, batched):
+        assert s2.time == p.steps
+        assert rel_l2(s2.populations(), s1.populations()) <= 1e-6
+        assert rel_l2(s2.far_field(th), s1.far_field(th)) <= 1e-6
+    batch.close()
+
+
+def test_batch_partial_steps_then_single_steps():
+    """A batch run can stop part way; single steps continue from its state."""
+    from paper_2510_11042_gb300 import lbem
+    probs = problems()[:2]
+    ref = [gpu_solver(p, steps=101) for p in probs]
+    sol = [gpu_solver(p, steps=0) for p in probs]
+    batch = lbem.Batch(sol)
+    batch.run([60, 37], autotune=False)
+    sol[0].step(41)
+    sol[1].step(64)
+    for a, b in zip(sol, ref):
+        assert a.time == b.time == 101
+        assert rel_l2(a.populations(), b.populations()) <= 1e-6
+    batch.close()
