@@ -41,6 +41,7 @@ class OrcParams(ctypes.Structure):
         ("dft_on", ctypes.c_int), ("dft_cos", ctypes.c_double), ("dft_sin", ctypes.c_double),
         ("dft_scale", ctypes.c_double), ("dft_acc", ctypes.POINTER(ctypes.c_double)),
         ("E_out", ctypes.POINTER(ctypes.c_double)), ("H_out", ctypes.POINTER(ctypes.c_double)),
+        ("u_out", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -65,6 +66,14 @@ def lib():
         _LIB.orc_sigma.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         _LIB.orc_ramp.restype = ctypes.c_double
         _LIB.orc_ramp.argtypes = [ctypes.c_double, ctypes.c_double]
+        _LIB.orc_collide_adjoint_cell.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_void_p]
+        _LIB.orc_collide_deps_cell.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+        _LIB.orc_adjoint_step.restype = ctypes.c_int
+        _LIB.orc_adjoint_step.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _LIB.orc_stream.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_void_p]
+        _LIB.orc_stream_adjoint.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_void_p]
         _LIB.orc_energy.restype = ctypes.c_double
         _LIB.orc_energy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p]
@@ -104,6 +113,20 @@ def collide_cell(f, eps=1.0, mu=1.0):
     f = _arr(f, NQ)
     out = np.zeros(NQ)
     lib().orc_collide_cell(f.ctypes.data, float(eps), float(mu), out.ctypes.data)
+    return out
+
+
+def collide_adjoint_cell(m, eps=1.0, mu=1.0):
+    m = _arr(m, NQ)
+    out = np.zeros(NQ)
+    lib().orc_collide_adjoint_cell(m.ctypes.data, float(eps), float(mu), out.ctypes.data)
+    return out
+
+
+def collide_deps_cell(f, eps=1.0):
+    f = _arr(f, NQ)
+    out = np.zeros(NQ)
+    lib().orc_collide_deps_cell(f.ctypes.data, float(eps), out.ctypes.data)
     return out
 
 
@@ -197,6 +220,37 @@ class Lattice:
         if rc != 0:
             raise MemoryError("oracle step failed")
         self.f = out
+
+    def record_pulled(self, on=True):
+        """Keep the pulled (post-stream, post-TF/SF) state of the next step in self.u."""
+        self.u = np.zeros((self.ncell, NQ)) if on else None
+        self.p.u_out = _dptr(self.u)
+
+    def stream(self, f):
+        f = np.ascontiguousarray(f, np.float64)
+        out = np.empty_like(f)
+        lib().orc_stream(ctypes.byref(self.p), f.ctypes.data, out.ctypes.data)
+        return out
+
+    def stream_adjoint(self, nu):
+        nu = np.ascontiguousarray(nu, np.float64)
+        out = np.empty_like(nu)
+        lib().orc_stream_adjoint(ctypes.byref(self.p), nu.ctypes.data, out.ctypes.data)
+        return out
+
+    def adjoint_step(self, lam_in, u, src, grad):
+        """lambda(n) from lambda(n+1); accumulates dJ/deps_r into grad."""
+        lam_in = np.ascontiguousarray(lam_in, np.float64)
+        u = np.ascontiguousarray(u, np.float64)
+        src_a = None if src is None else np.ascontiguousarray(src, np.float64)
+        out = np.empty_like(lam_in)
+        assert grad.dtype == np.float64 and grad.flags.c_contiguous
+        rc = lib().orc_adjoint_step(ctypes.byref(self.p), lam_in.ctypes.data, u.ctypes.data,
+                                    None if src_a is None else src_a.ctypes.data, out.ctypes.data,
+                                    grad.ctypes.data)
+        if rc != 0:
+            raise MemoryError("oracle adjoint step failed")
+        return out
 
     def energy(self):
         n = (ctypes.c_int * 3)(*self.shape)

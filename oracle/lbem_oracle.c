@@ -72,6 +72,9 @@ typedef struct {
     double *dft_acc;          /* [ncell][6][2]: Ex Ey Ez Hx Hy Hz, (re, im) */
     /* optional field output at t = n+1 (pre-collision moments) */
     double *E_out, *H_out;    /* [ncell][3] each, may be NULL */
+    /* optional output of the pulled populations (after streaming and TF/SF,
+       before collision), [ncell][42]; used by the adjoint */
+    double *u_out;
 } orc_params;
 
 static void cross3(const double a[3], const double b[3], double out[3])
@@ -240,6 +243,8 @@ int orc_step(const orc_params *p, const double *fin, double *fout, int64_t n)
         }
     }
 
+    if (p->u_out) memcpy(p->u_out, f, ncell * ORC_NQ * sizeof(double));
+
     /* 3-6. moments, DFT, collision, absorbing layer */
 #pragma omp parallel for schedule(static)
     for (long long cell = 0; cell < (long long)ncell; ++cell) {
@@ -296,4 +301,156 @@ double orc_energy(const int n[3], const double *eps, const double *mu, const dou
     return total;
 }
 
-int orc_abi_version(void) { return 1; }
+/* ------------------------------------------------------------------------
+ * Discrete adjoint of the step (for gradients with respect to eps_r).
+ * The step is f(n+1) = K C_eps S f(n) + (terms independent of f), with S the
+ * clamped pull, C_eps the per-cell collision and K the absorbing-layer
+ * factors, so the adjoint state obeys lambda(n) = S^T C_eps^T K lambda(n+1)
+ * (plus the sensitivity of the objective to the fields of step n).
+ * ------------------------------------------------------------------------ */
+
+/* C_eps^T applied to one cell's vector: C = 2 F_eq - I with F_eq the linear
+ * map f -> f_eq(E(f), H(f)) of Eq. 2 (E = D/eps, H = B/mu); its transpose
+ * gathers every output's weight back onto D and B:
+ *   a_d = dE/dD * [2 (eps-1) m_e0 + sum_i (m_ei + m_hi x c_i) / 3]   (mu = 1: h_0 term 0)
+ *   b_d = dH/dB * [2 (mu-1) m_h0 + sum_i (m_hi - m_ei x c_i) / 3]
+ * and (C^T m)_q = a_comp(q) (e-family) or b_comp(q) (h-family) minus m_q.  The
+ * dot-product test <C x, y> = <x, C^T y> pins it against orc_collide_cell. */
+void orc_collide_adjoint_cell(const double m[ORC_NQ], double eps, double mu, double out[ORC_NQ])
+{
+    double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int i = 0; i < 7; ++i) {
+        double c[3] = {(double)VEL[i][0], (double)VEL[i][1], (double)VEL[i][2]};
+        const double *me = m + (0 * 7 + i) * 3, *mh = m + (1 * 7 + i) * 3;
+        if (i == 0) {
+            for (int d = 0; d < 3; ++d) {
+                a[d] += 2.0 * (eps - 1.0) * me[d];
+                b[d] += 2.0 * (mu - 1.0) * mh[d];
+            }
+            continue;
+        }
+        double mhxc[3], mexc[3];
+        cross3(mh, c, mhxc);
+        cross3(me, c, mexc);
+        for (int d = 0; d < 3; ++d) {
+            a[d] += (me[d] + mhxc[d]) / 3.0;
+            b[d] += (mh[d] - mexc[d]) / 3.0;
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        a[d] /= eps;   /* E = D / eps */
+        b[d] /= mu;    /* H = B / mu  */
+    }
+    for (int i = 0; i < 7; ++i)
+        for (int d = 0; d < 3; ++d) {
+            out[(0 * 7 + i) * 3 + d] = a[d] - m[(0 * 7 + i) * 3 + d];
+            out[(1 * 7 + i) * 3 + d] = b[d] - m[(1 * 7 + i) * 3 + d];
+        }
+}
+
+/* d(C_eps f)/d eps for one cell (E = D/eps, dE/deps = -D/eps^2):
+ *   e_0: 2 d[(eps-1) E]/deps = 2 D / eps^2,   e_i: -(D / eps^2) / 3,
+ *   h_i: -(c_i x D / eps^2) / 3,              h_0: 0. */
+void orc_collide_deps_cell(const double f[ORC_NQ], double eps, double out[ORC_NQ])
+{
+    double D[3] = {0, 0, 0};
+    for (int i = 0; i < 7; ++i)
+        for (int d = 0; d < 3; ++d) D[d] += f[(0 * 7 + i) * 3 + d];
+    double g[3];
+    for (int d = 0; d < 3; ++d) g[d] = D[d] / (eps * eps);
+    for (int i = 0; i < 7; ++i) {
+        double c[3] = {(double)VEL[i][0], (double)VEL[i][1], (double)VEL[i][2]}, cxg[3];
+        cross3(c, g, cxg);
+        for (int d = 0; d < 3; ++d) {
+            out[(0 * 7 + i) * 3 + d] = (i == 0) ? 2.0 * g[d] : -g[d] / 3.0;
+            out[(1 * 7 + i) * 3 + d] = (i == 0) ? 0.0 : -cxg[d] / 3.0;
+        }
+    }
+}
+
+/* One adjoint step.  lam_in = lambda(n+1) [ncell][42]; u = the pulled state of
+ * forward step n (orc_params.u_out); src (optional) = dJ/du(n) [ncell][42],
+ * the objective's sensitivity to the pulled populations of step n; grad
+ * accumulates dJ/deps_r per cell.  lam_out = lambda(n) = S^T (C^T K lam_in +
+ * src), with S^T the literal scatter of the clamped pull:
+ * lam_out_i(clamp(r - c_i)) += nu_i(r). */
+int orc_adjoint_step(const orc_params *p, const double *lam_in, const double *u, const double *src,
+                     double *lam_out, double *grad)
+{
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const size_t ncell = (size_t)nx * ny * nz;
+    double *nu = (double *)malloc(ncell * ORC_NQ * sizeof(double));
+    if (!nu) return -1;
+#pragma omp parallel for schedule(static)
+    for (long long cell = 0; cell < (long long)ncell; ++cell) {
+        int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((size_t)nx * ny));
+        int g[3] = {x + p->origin[0], y + p->origin[1], z + p->origin[2]};
+        double keep = 1.0 - orc_sigma(g, p->gn, p->sponge_w, p->sigma_max);
+        double eps = p->eps[cell], mu = p->mu ? p->mu[cell] : 1.0;
+        double m[ORC_NQ], ct[ORC_NQ], dc[ORC_NQ];
+        for (int q = 0; q < ORC_NQ; ++q) m[q] = keep * lam_in[cell * ORC_NQ + q];
+        orc_collide_adjoint_cell(m, eps, mu, ct);
+        orc_collide_deps_cell(u + cell * ORC_NQ, eps, dc);
+        double gsum = 0.0;
+        for (int q = 0; q < ORC_NQ; ++q) gsum += m[q] * dc[q];
+        grad[cell] += gsum;
+        for (int q = 0; q < ORC_NQ; ++q)
+            nu[cell * ORC_NQ + q] = ct[q] + (src ? src[cell * ORC_NQ + q] : 0.0);
+    }
+    memset(lam_out, 0, ncell * ORC_NQ * sizeof(double));
+    for (size_t cell = 0; cell < ncell; ++cell) {
+        int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((size_t)nx * ny));
+        for (int fam = 0; fam < 2; ++fam)
+            for (int i = 0; i < 7; ++i) {
+                int sx = src_coord(x, VEL[i][0], nx, p->periodic);
+                int sy = src_coord(y, VEL[i][1], ny, p->periodic);
+                int sz = src_coord(z, VEL[i][2], nz, p->periodic);
+                size_t s = ((size_t)sz * ny + sy) * nx + sx;
+                for (int a = 0; a < 3; ++a) {
+                    int q = (fam * 7 + i) * 3 + a;
+                    lam_out[s * ORC_NQ + q] += nu[cell * ORC_NQ + q];
+                }
+            }
+    }
+    free(nu);
+    return 0;
+}
+
+/* The pull alone (no collision), for the dot-product test of the scatter. */
+void orc_stream(const orc_params *p, const double *fin, double *fout)
+{
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const size_t ncell = (size_t)nx * ny * nz;
+    for (size_t cell = 0; cell < ncell; ++cell) {
+        int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((size_t)nx * ny));
+        for (int fam = 0; fam < 2; ++fam)
+            for (int i = 0; i < 7; ++i) {
+                size_t s = ((size_t)src_coord(z, VEL[i][2], nz, p->periodic) * ny +
+                            src_coord(y, VEL[i][1], ny, p->periodic)) * nx +
+                           src_coord(x, VEL[i][0], nx, p->periodic);
+                for (int a = 0; a < 3; ++a)
+                    fout[cell * ORC_NQ + (fam * 7 + i) * 3 + a] = fin[s * ORC_NQ + (fam * 7 + i) * 3 + a];
+            }
+    }
+}
+
+/* The scatter S^T alone (the adjoint of orc_stream). */
+void orc_stream_adjoint(const orc_params *p, const double *nu, double *out)
+{
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const size_t ncell = (size_t)nx * ny * nz;
+    memset(out, 0, ncell * ORC_NQ * sizeof(double));
+    for (size_t cell = 0; cell < ncell; ++cell) {
+        int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((size_t)nx * ny));
+        for (int fam = 0; fam < 2; ++fam)
+            for (int i = 0; i < 7; ++i) {
+                size_t s = ((size_t)src_coord(z, VEL[i][2], nz, p->periodic) * ny +
+                            src_coord(y, VEL[i][1], ny, p->periodic)) * nx +
+                           src_coord(x, VEL[i][0], nx, p->periodic);
+                for (int a = 0; a < 3; ++a)
+                    out[s * ORC_NQ + (fam * 7 + i) * 3 + a] += nu[cell * ORC_NQ + (fam * 7 + i) * 3 + a];
+            }
+    }
+}
+
+int orc_abi_version(void) { return 2; }
