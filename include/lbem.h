@@ -233,6 +233,41 @@ int64_t lbem_batch_launches(lbem_batch b);
 const char *lbem_batch_last_error(lbem_batch b);
 void lbem_batch_destroy(lbem_batch b);
 
+/* Gradient of far-field intensities with respect to the permittivity map: the
+ * discrete adjoint of lbem_step (the paper's scheme is linear in the
+ * populations for a fixed eps_r map, so the adjoint of each step is its
+ * transpose; the paper itself computes no gradients).  The objective is
+ *   J = sum_k weights[k] |S(theta_k, phi_k)|^2     (|S|^2 of lbem_far_field)
+ * and the result is dJ/deps_r for every cell, through every step of the run:
+ * collision (Eqs. 1-2), clamped streaming (Eq. 4), the TF/SF source, the
+ * absorbing layer and the DFT window (|E_I| does not depend on eps_r).
+ * FP32 storage only (LBEM_ERR_ARG otherwise).
+ *
+ * lbem_forward_checkpointed(h, n_steps, K, ...) replaces lbem_step for a run
+ * that is to be differentiated: it must start at t = 0 (right after
+ * lbem_inject_plane_wave, with the DFT window set) and takes n_steps steps,
+ * keeping the state at every K-th step in its workspace
+ * (lbem_adjoint_workspace_bytes; NULL: the library allocates it and frees it
+ * with the handle).  The workspace holds ceil(n_steps / K) checkpoints of the
+ * populations plus K steps of recorded fields (NE floats per cell and step),
+ * so K ~ sqrt(n_steps * populations / NE) minimises it.
+ *
+ * lbem_adjoint then replays each segment forward from its checkpoint and runs
+ * the adjoint steps backwards through it: about two more steps' worth of work
+ * per step.  theta, phi (phi may be NULL in 2D), weights: n_ang (1..1024) host
+ * doubles.  grad_out: nx*ny*nz floats, x fastest, on the device when
+ * grad_on_device, else host memory.  J_out (host, optional): the objective.
+ * It may be called again with other angles or weights; lbem_set_permittivity,
+ * lbem_inject_plane_wave, lbem_set_dft_window, lbem_set_populations and
+ * lbem_load_state discard the checkpoints (then LBEM_ERR_STATE).  The DFT
+ * window must lie inside the checkpointed steps.  Synchronous. */
+int32_t lbem_adjoint_workspace_bytes(lbem_handle h, int64_t n_steps, int32_t K, size_t *bytes_out);
+int32_t lbem_forward_checkpointed(lbem_handle h, int64_t n_steps, int32_t K, void *workspace,
+                                  size_t workspace_bytes);
+int32_t lbem_adjoint(lbem_handle h, const double *theta_host, const double *phi_host,
+                     const double *weights_host, int32_t n_ang, float *grad_out,
+                     int32_t grad_on_device, double *J_out);
+
 /* Far-field projection that allocates nothing (the paper has no counterpart;
  * this is a library convenience).  For callers that cannot call cudaMalloc or
  * any allocator -- e.g. a host application that owns the device memory budget

@@ -51,6 +51,13 @@ struct lbem_ctx {
     int dft_periods = 0;
     float scale = 1.f, inv_scale = 1.f;  // stored population = population / scale
     int64_t launches = 0;
+    // adjoint: checkpoints of lbem_forward_checkpointed and the backward buffers
+    char *adj_ws = nullptr;
+    size_t adj_bytes = 0;
+    bool adj_owns = false;
+    bool adj_valid = false;
+    int64_t adj_steps = 0;
+    int adj_K = 0;
     char err[512];
 };
 
@@ -346,6 +353,7 @@ int32_t lbem_set_permittivity(lbem_handle h, const float *eps_r, int32_t eps_on_
 {
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
     if (!eps_r) return fail(h, LBEM_ERR_ARG, "eps_r is NULL");
+    h->adj_valid = false;
     return upload_eps(h, eps_r, eps_on_device);
 }
 
@@ -439,6 +447,7 @@ int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
         h->launches += 1;
         CK(h, cudaStreamSynchronize(h->stream));
     }
+    h->adj_valid = false;
     h->wave = *w;
     h->wave.source_index = src;
     h->has_wave = true;
@@ -470,6 +479,7 @@ int32_t lbem_set_dft_window(lbem_handle h, int64_t t_start, int32_t n_periods)
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
     if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
     if (n_periods < 1 || t_start < 1) return fail(h, LBEM_ERR_ARG, "need t_start >= 1 and n_periods >= 1");
+    h->adj_valid = false;
     h->dft_t0 = t_start;
     h->dft_periods = n_periods;
     CK(h, cudaMemsetAsync(h->dft, 0, h->dft_doubles * 8, h->stream));
@@ -526,6 +536,13 @@ struct lbem_batch_ctx {
     int tuned = 0, best_bps = 0, best_rpi = 1;
     double best_ms = 0.0;
     int64_t launches = 0;
+    // adjoint: checkpoints of lbem_forward_checkpointed and the backward buffers
+    char *adj_ws = nullptr;
+    size_t adj_bytes = 0;
+    bool adj_owns = false;
+    bool adj_valid = false;
+    int64_t adj_steps = 0;
+    int adj_K = 0;
     char err[512];
 };
 
@@ -865,6 +882,7 @@ int32_t lbem_get_populations(lbem_handle h, float *out, int32_t on_device)
 int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t on_device)
 {
     if (!h || !in) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    h->adj_valid = false;
     for (int q = 0; q < h->Q; ++q) {
         const float *src = in + (size_t)q * h->ncell;
         if (!on_device) {
@@ -989,6 +1007,7 @@ int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
     if (std::memcmp(hd.magic, "LBEMSTA1", 8) || hd.nx != h->g.nx || hd.ny != h->g.ny || hd.nz != h->g.nz ||
         hd.mode != h->g.mode || hd.storage != h->g.storage || hd.Q != h->Q)
         return fail(h, LBEM_ERR_ARG, "snapshot does not match this grid");
+    h->adj_valid = false;
     const char *p = (const char *)buf + sizeof hd;
     CK(h, cudaMemcpyAsync(h->f[h->cur], p, hd.pop_bytes, cudaMemcpyHostToDevice, h->stream));
     p += hd.pop_bytes;
@@ -1048,11 +1067,281 @@ int32_t lbem_sync(lbem_handle h)
 void lbem_destroy(lbem_handle h)
 {
     if (!h) return;
-    if (h->owns_ws && h->ws) {
-        cudaStreamSynchronize(h->stream);
-        cudaFree(h->ws);
-    }
+    if ((h->owns_ws && h->ws) || (h->adj_owns && h->adj_ws)) cudaStreamSynchronize(h->stream);
+    if (h->owns_ws && h->ws) cudaFree(h->ws);
+    if (h->adj_owns && h->adj_ws) cudaFree(h->adj_ws);
     delete h;
+}
+
+// ------------------------------------------------------------ adjoint
+// Workspace of lbem_forward_checkpointed / lbem_adjoint:
+//   checkpoints  one per segment of K steps: populations and the three incident-line buffers
+//   replay       two population buffers and three line buffers for the forward replay
+//   mu           two adjoint population buffers
+//   rec          total-field D of every step of one segment (K x NE planes)
+//   G            dJ/dX per DFT entry (DFT array layout)
+//   grad         FP64 accumulator of dJ/d(1/eps_r), one per padded cell
+//   gamma, wts   per-angle sensitivities and weights
+struct AdjLayout {
+    size_t ck0, ck_stride, ck_lines, rf[2], rline[3], mu[2], rec, G, grad, gamma, wts, total;
+    int nseg;
+};
+
+static AdjLayout adj_layout(const lbem_ctx *h, int64_t n_steps, int K)
+{
+    AdjLayout L;
+    const size_t pop = (size_t)h->Q * h->P * 4;
+    const size_t line = (size_t)h->Q * h->n_line_max * 4;
+    const int NE = h->g.mode == 0 ? 1 : (h->g.mode == 1 ? 2 : 3);
+    L.nseg = (int)((n_steps + K - 1) / K);
+    L.ck_lines = align256(pop);
+    L.ck_stride = L.ck_lines + 3 * align256(line);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.ck0 = take(L.ck_stride * (size_t)L.nseg);
+    for (int k = 0; k < 2; ++k) L.rf[k] = take(pop);
+    for (int k = 0; k < 3; ++k) L.rline[k] = take(line);
+    for (int k = 0; k < 2; ++k) L.mu[k] = take(pop);
+    L.rec = take((size_t)K * NE * h->P * 4);
+    L.G = take(h->dft_doubles_max * 8);
+    L.grad = take((size_t)h->P * 8);
+    L.gamma = take((size_t)kAngleBatch * 12 * 8);
+    L.wts = take((size_t)kAngleBatch * 8);
+    L.total = o;
+    return L;
+}
+
+int32_t lbem_adjoint_workspace_bytes(lbem_handle h, int64_t n_steps, int32_t K, size_t *bytes)
+{
+    if (!h || !bytes) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    if (n_steps < 1 || K < 1) return fail(h, LBEM_ERR_ARG, "need n_steps >= 1 and K >= 1");
+    *bytes = adj_layout(h, n_steps, K).total;
+    return LBEM_OK;
+}
+
+int32_t lbem_forward_checkpointed(lbem_handle h, int64_t n_steps, int32_t K, void *workspace,
+                                  size_t workspace_bytes)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (n_steps < 1 || K < 1) return fail(h, LBEM_ERR_ARG, "need n_steps >= 1 and K >= 1");
+    if (h->g.storage != LBEM_F32) return fail(h, LBEM_ERR_ARG, "the adjoint needs FP32 storage");
+    if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
+    if (h->t != 0) return fail(h, LBEM_ERR_STATE, "the checkpointed run must start at t = 0 (got t = %lld)",
+                               (long long)h->t);
+    if (workspace && ((uintptr_t)workspace & 255))
+        return fail(h, LBEM_ERR_ARG, "workspace must be 256-byte aligned");
+    const AdjLayout L = adj_layout(h, n_steps, K);
+    if (workspace && workspace_bytes < L.total)
+        return fail(h, LBEM_ERR_OOM, "adjoint workspace of %zu bytes is smaller than the %zu needed",
+                    workspace_bytes, L.total);
+    h->adj_valid = false;
+    if (h->adj_owns && h->adj_ws) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->adj_ws);
+    }
+    h->adj_ws = nullptr;
+    h->adj_owns = false;
+    if (workspace) {
+        h->adj_ws = (char *)workspace;
+        h->adj_bytes = workspace_bytes;
+    } else {
+        cudaError_t e = cudaMalloc((void **)&h->adj_ws, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->adj_ws = nullptr;
+            return fail(h, LBEM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", L.total, cudaGetErrorString(e));
+        }
+        h->adj_owns = true;
+        h->adj_bytes = L.total;
+    }
+    const size_t pop = (size_t)h->Q * h->P * 4;
+    const size_t line = (size_t)h->Q * h->n_line_max * 4;
+    for (int seg = 0; seg < L.nseg; ++seg) {
+        char *ck = h->adj_ws + L.ck0 + (size_t)seg * L.ck_stride;
+        CK(h, cudaMemcpyAsync(ck, h->f[h->cur], pop, cudaMemcpyDeviceToDevice, h->stream));
+        for (int k = 0; k < 3; ++k)
+            CK(h, cudaMemcpyAsync(ck + L.ck_lines + k * align256(line), h->line[k], line,
+                                  cudaMemcpyDeviceToDevice, h->stream));
+        const int64_t len = std::min<int64_t>(K, n_steps - (int64_t)seg * K);
+        const int rc = lbem_step(h, len);
+        if (rc != LBEM_OK) return rc;
+    }
+    h->adj_steps = n_steps;
+    h->adj_K = K;
+    h->adj_valid = true;
+    return LBEM_OK;
+}
+
+int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, const double *weights,
+                     int32_t n_ang, float *grad_out, int32_t grad_on_device, double *J_out)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (!h->adj_valid)
+        return fail(h, LBEM_ERR_STATE, "no checkpointed forward run for the current permittivity and window");
+    if (n_ang < 1 || n_ang > kAngleBatch || !theta || !weights || !grad_out)
+        return fail(h, LBEM_ERR_ARG, "need 1..%d angles with theta, weights and grad_out", kAngleBatch);
+    if (h->g.mode == 2 && !phi) return fail(h, LBEM_ERR_ARG, "3D needs phi");
+    const int64_t w_end = h->dft_t0 + (int64_t)h->dft_periods * h->T - 1;  // last field time in the window
+    if (h->dft_t0 < 1 || w_end > h->adj_steps || w_end > h->t)
+        return fail(h, LBEM_ERR_STATE, "the DFT window must lie inside the checkpointed run");
+    const AdjLayout L = adj_layout(h, h->adj_steps, h->adj_K);
+    char *W = h->adj_ws;
+    const int NE = h->g.mode == 0 ? 1 : (h->g.mode == 1 ? 2 : 3);
+    const size_t pop = (size_t)h->Q * h->P * 4;
+    const size_t line = (size_t)h->Q * h->n_line_max * 4;
+
+    // 1. far field of the angles: N, L and |S|^2
+    FarFieldArgs fa;
+    std::memset(&fa, 0, sizeof fa);
+    fa.dft = h->dft;
+    fa.line_dft = h->line_dft;
+    fa.g = h->faces;
+    fa.mode = h->g.mode;
+    fa.k = 2.0 * M_PI / h->wave.wavelength;
+    for (int c = 0; c < 3; ++c) {
+        fa.center[c] = h->wave.center[c];
+        fa.pol[c] = h->wave.pol[c];
+    }
+    centre_nodes(h, &fa.center_i0, &fa.center_i1);
+    const long long cells = h->faces.cell_start[h->faces.nfaces];
+    fa.chunks = std::max(1, std::min(kMaxChunks, (int)((cells + 4095) / 4096)));
+    double *d_theta = h->scratch;
+    double *d_phi = d_theta + kAngleBatch;
+    double *d_s2 = d_phi + kAngleBatch;
+    double *d_amp = d_s2 + kAngleBatch;
+    double *d_part = d_amp + (size_t)kAngleBatch * 12;
+    CK(h, cudaMemcpyAsync(d_theta, theta, n_ang * 8, cudaMemcpyHostToDevice, h->stream));
+    if (h->g.mode == 2) CK(h, cudaMemcpyAsync(d_phi, phi, n_ang * 8, cudaMemcpyHostToDevice, h->stream));
+    double *d_w = (double *)(W + L.wts);
+    CK(h, cudaMemcpyAsync(d_w, weights, n_ang * 8, cudaMemcpyHostToDevice, h->stream));
+    fa.theta = d_theta;
+    fa.phi = d_phi;
+    fa.n_ang = n_ang;
+    fa.partial = d_part;
+    fa.s2 = d_s2;
+    fa.amp = d_amp;
+    int l = 0;
+    CK(h, launch_far_field(fa, h->stream, &l));
+    h->launches += l;
+
+    // 2. dJ/dX of every DFT entry
+    AdjWeightArgs wa;
+    std::memset(&wa, 0, sizeof wa);
+    wa.g = h->faces;
+    wa.mode = h->g.mode;
+    wa.n_ang = n_ang;
+    wa.theta = d_theta;
+    wa.phi = d_phi;
+    wa.weights = d_w;
+    wa.amp = d_amp;
+    wa.line_dft = h->line_dft;
+    wa.k = fa.k;
+    for (int c = 0; c < 3; ++c) {
+        wa.center[c] = fa.center[c];
+        wa.pol[c] = fa.pol[c];
+    }
+    wa.center_i0 = fa.center_i0;
+    wa.center_i1 = fa.center_i1;
+    wa.gamma = (double *)(W + L.gamma);
+    wa.G = (double *)(W + L.G);
+    CK(h, cudaMemsetAsync(wa.G, 0, h->dft_doubles * 8, h->stream));
+    CK(h, launch_adjoint_weights(wa, h->stream, &l));
+    h->launches += l;
+
+    // 3. segments backwards: replay the forward run from the checkpoint with
+    //    D^F recorded, then the adjoint steps of the segment
+    float *mu[2] = {(float *)(W + L.mu[0]), (float *)(W + L.mu[1])};
+    float *rf[2] = {(float *)(W + L.rf[0]), (float *)(W + L.rf[1])};
+    float *rline[3] = {(float *)(W + L.rline[0]), (float *)(W + L.rline[1]), (float *)(W + L.rline[2])};
+    float *rec = (float *)(W + L.rec);
+    double *grad = (double *)(W + L.grad);
+    CK(h, cudaMemsetAsync(mu[0], 0, pop, h->stream));
+    CK(h, cudaMemsetAsync(grad, 0, (size_t)h->P * 8, h->stream));
+    int mcur = 0;
+    const double scale = 2.0 / ((double)h->dft_periods * h->T);
+
+    StepArgs a;
+    fill_common_args(h, a);
+    a.dft_on = 0;
+    AdjointArgs b;
+    std::memset(&b, 0, sizeof b);
+    b.inv_eps = h->inv_eps;
+    b.grad = grad;
+    b.nx = h->g.nx; b.ny = h->g.ny; b.nz = h->g.nz; b.nxp = h->nxp;
+    b.P = h->P;
+    b.w = h->g.absorber_width;
+    b.sigma_max = (float)h->g.sigma_max;
+    b.inv_w = b.w > 0 ? 1.0f / (float)b.w : 0.f;
+    for (int k = 0; k < 3; ++k) {
+        b.nt_lo[k] = h->wave.ntff_lo[k];
+        b.nt_hi[k] = h->wave.ntff_hi[k];
+    }
+    b.G = wa.G;
+    for (int f = 0; f < h->faces.nfaces; ++f) {
+        b.face_off[f] = h->faces.off[f];
+        b.face_nu[f] = h->faces.nu[f];
+        b.face_nv[f] = h->faces.nv[f];
+    }
+    b.dft_scale = scale;
+
+    for (int seg = L.nseg - 1; seg >= 0; --seg) {
+        const int64_t t0 = (int64_t)seg * h->adj_K;
+        const int64_t len = std::min<int64_t>(h->adj_K, h->adj_steps - t0);
+        const char *ck = W + L.ck0 + (size_t)seg * L.ck_stride;
+        CK(h, cudaMemcpyAsync(rf[0], ck, pop, cudaMemcpyDeviceToDevice, h->stream));
+        for (int k = 0; k < 3; ++k)
+            CK(h, cudaMemcpyAsync(rline[k], ck + L.ck_lines + k * align256(line), line,
+                                  cudaMemcpyDeviceToDevice, h->stream));
+        for (int64_t k = 0; k < len; ++k) {
+            const int64_t t = t0 + k;   // state time before the step
+            for (int q = 0; q < h->Q; ++q) {
+                a.fin_q[q] = rf[k & 1] + (size_t)q * h->P;
+                a.fout_q[q] = rf[(k & 1) ^ 1] + (size_t)q * h->P;
+            }
+            a.line_n = rline[t % 3];
+            a.line_n1 = rline[(t + 1) % 3];
+            a.line_out = rline[(t + 2) % 3];
+            source_fields(h, t + 2, a.src_E, a.src_H);
+            a.rec = rec + (size_t)k * NE * h->P;
+            cudaError_t e = launch_step_record(h->g.mode, a, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "replay step launch");
+            h->launches += 1;
+        }
+        for (int64_t k = len - 1; k >= 0; --k) {
+            const int64_t tf = t0 + k + 1;   // time of the fields of this step
+            for (int q = 0; q < h->Q; ++q) {
+                b.lin_q[q] = mu[mcur] + (size_t)q * h->P;
+                b.lout_q[q] = mu[mcur ^ 1] + (size_t)q * h->P;
+            }
+            b.rec = rec + (size_t)k * NE * h->P;
+            b.dft_on = tf >= h->dft_t0 && tf <= w_end;
+            if (b.dft_on) {
+                const double ph = 2.0 * M_PI * (double)(tf % h->T) / (double)h->T;
+                b.dft_c = std::cos(ph);
+                b.dft_s = std::sin(ph);
+            }
+            cudaError_t e = launch_adjoint_step(h->g.mode, b, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
+            h->launches += 1;
+            mcur ^= 1;
+        }
+    }
+
+    // 4. dJ/deps_r and J
+    float *out = grad_on_device ? grad_out : h->stage;
+    CK(h, launch_adjoint_finalize(grad, h->inv_eps, h->g.nx, h->g.ny, h->g.nz, h->nxp, out, h->stream));
+    h->launches += 1;
+    if (!grad_on_device)
+        CK(h, cudaMemcpyAsync(grad_out, h->stage, (size_t)h->ncell * 4, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<double> s2(n_ang);
+    CK(h, cudaMemcpyAsync(s2.data(), d_s2, n_ang * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (J_out) {
+        double J = 0.0;
+        for (int i = 0; i < n_ang; ++i) J += weights[i] * s2[i];
+        *J_out = J;
+    }
+    return check_status(h);
 }
 
 const char *lbem_last_error(lbem_handle h) { return h ? h->err : g_create_err; }

@@ -51,6 +51,57 @@ template <int MODE> struct Planes {
 inline int planes_of_mode(int mode) { return mode == 2 ? 42 : 21; }
 inline int dft_comps_of_mode(int mode) { return mode == 2 ? 6 : 3; }
 
+// ------------------------------------------------ device helpers shared by
+// the step, adjoint and observable kernels
+// x/3 to within rounding: the constant 1/3 split into a float and a remainder,
+// x*hi + x*lo evaluated with one rounding (FMA).  A plain x * fl(1/3) is biased
+// upwards (fl(1/3) > 1/3), which would make the collision grow D and B by
+// ~2e-8 per step; this form is unbiased.
+__device__ __forceinline__ float third(float x)
+{
+    constexpr float hi = 0.333333343267f;        // fl(1/3)
+    constexpr float lo = -9.934107481e-09f;      // 1/3 - fl(1/3)
+    return fmaf(x, hi, x * lo);
+}
+
+// Direction i = 0..6: rest, +x, -x, +y, -y, +z, -z.
+__host__ __device__ constexpr int dir_axis(int i) { return i == 0 ? -1 : (i - 1) / 2; }
+__host__ __device__ constexpr int dir_sign(int i) { return i == 0 ? 0 : ((i & 1) ? 1 : -1); }
+
+// (c_i x V)_a for an axis-aligned unit velocity c_i.
+__device__ __forceinline__ float cross_c(int i, const float V[3], int a)
+{
+    const int d = dir_axis(i);
+    const float s = (float)dir_sign(i);
+    // e_x x V = (0, -Vz, Vy), e_y x V = (Vz, 0, -Vx), e_z x V = (-Vy, Vx, 0)
+    if (d == 0) return a == 0 ? 0.f : (a == 1 ? -s * V[2] : s * V[1]);
+    if (d == 1) return a == 0 ? s * V[2] : (a == 1 ? 0.f : -s * V[0]);
+    return a == 0 ? -s * V[1] : (a == 1 ? s * V[0] : 0.f);
+}
+
+__device__ __forceinline__ float layer_keep(int d, int w, float sigma_max, float inv_w)
+{
+    if (d >= w) return 1.f;
+    const float m = (float)(w - d) * inv_w;
+    return 1.f - sigma_max * m * m * m;
+}
+
+__device__ __forceinline__ bool in_box(int x, int y, int z, const int lo[3], const int hi[3])
+{
+    return x >= lo[0] && x <= hi[0] && y >= lo[1] && y <= hi[1] && z >= lo[2] && z <= hi[2];
+}
+
+// DFT slot of field component c (0..2) in each mode, or -1 when the mode does
+// not carry it: EZ (E_z, H_x, H_y), HZ (E_x, E_y, H_z), 3D (E_x..E_z, H_x..H_z).
+__host__ __device__ constexpr int slot_E(int mode, int c)
+{
+    return mode == 0 ? (c == 2 ? 0 : -1) : (mode == 1 ? (c < 2 ? c : -1) : c);
+}
+__host__ __device__ constexpr int slot_H(int mode, int c)
+{
+    return mode == 0 ? (c < 2 ? 1 + c : -1) : (mode == 1 ? (c == 2 ? 2 : -1) : 3 + c);
+}
+
 // Arguments of the fused step kernel (passed by value).
 struct StepArgs {
     const void *fin_q[kMaxQ];  // start of each input population plane
@@ -90,6 +141,10 @@ struct StepArgs {
     double *line_dft;          // [n_line][3][2]
     // reduced-precision storage: stored = population / scale (power of two)
     float scale, inv_scale;
+    // forward replay for the adjoint: total-field D of the pulled populations
+    // (scattered D plus the incident D inside the total-field box), NE planes
+    // of P floats, written only by the recording kernel
+    float *rec;
 };
 
 // One problem of a batched run (device copy; see lbem_batch_run).
@@ -127,6 +182,8 @@ cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cu
 int batch_max_blocks_per_sm(int mode, int storage);
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_line_init(int mode, const StepArgs &a, cudaStream_t s);
+// The step kernel with a.rec written (FP32 storage; forward replay of the adjoint)
+cudaError_t launch_step_record(int mode, const StepArgs &a, cudaStream_t s);
 
 // Where the stored populations hold the scattered part G = F - I (inside the
 // total-field box), diagnostics add the incident line back.
@@ -184,5 +241,51 @@ cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv
                           float scale, long long P, int nx, int ny, int nz, int nxp,
                           const IncView &inc, double *partial, int max_partial, double *out,
                           cudaStream_t s, int *launches);
+
+// ---------------------------------------------------------------- adjoint
+// One backward step of the discrete adjoint (adjoint.cu).  lin_q holds
+// mu(t+1) = dJ/du(t+1), the objective's sensitivity to the pulled populations
+// of the next step; the kernel writes mu(t) and adds this step's term of
+// dJ/d(1/eps_r) to grad.  FP32 populations; FP64 gradient accumulator.
+struct AdjointArgs {
+    const float *lin_q[kMaxQ];
+    float *lout_q[kMaxQ];
+    const float *inv_eps;
+    const float *rec;          // total-field D of step t's pulled state, NE planes of P
+    double *grad;              // [P]
+    int nx, ny, nz, nxp;
+    long long P;
+    int nblk_x;
+    int w;
+    float sigma_max, inv_w;
+    // sensitivity of J to the DFT samples of step t (fields at time t)
+    int dft_on;
+    double dft_c, dft_s, dft_scale;
+    int nt_lo[3], nt_hi[3];
+    const double *G;           // dJ/dX per DFT entry, complex, in the DFT array layout
+    long long face_off[kMaxFaces];
+    int face_nu[kMaxFaces], face_nv[kMaxFaces];
+};
+
+// Sensitivity of J = sum_k w_k |S(theta_k, phi_k)|^2 to the DFT phasors.
+struct AdjWeightArgs {
+    FaceGeom g;
+    int mode;
+    int n_ang;
+    const double *theta, *phi, *weights;
+    const double *amp;         // [n_ang][12]: N and L of each angle (far_field_finalize)
+    const double *line_dft;
+    double k;
+    double center[3];
+    double pol[3];
+    int center_i0, center_i1;
+    double *gamma;             // [n_ang][12]: dJ/dN, dJ/dL (complex) of each angle
+    double *G;                 // output, DFT layout
+};
+
+cudaError_t launch_adjoint_step(int mode, const AdjointArgs &a, cudaStream_t s);
+cudaError_t launch_adjoint_weights(const AdjWeightArgs &a, cudaStream_t s, int *launches);
+cudaError_t launch_adjoint_finalize(const double *grad, const float *inv_eps, int nx, int ny, int nz,
+                                    int nxp, float *out, cudaStream_t s);
 
 }  // namespace lbem

@@ -33,17 +33,6 @@ __device__ __forceinline__ double warp_sum(double v)
 // ------------------------------------------------------------ far field
 // Stage 1: one block per (chunk, angle) sums w J e^{j phi}, w M e^{j phi} over
 // its share of the face cells; writes 12 doubles (Re/Im of N_xyz, L_xyz).
-// DFT slot of field component c (0..2) in each mode, or -1 when the mode does
-// not carry it: EZ (E_z, H_x, H_y), HZ (E_x, E_y, H_z), 3D (E_x..E_z, H_x..H_z).
-__host__ __device__ constexpr int slot_E(int mode, int c)
-{
-    return mode == 0 ? (c == 2 ? 0 : -1) : (mode == 1 ? (c < 2 ? c : -1) : c);
-}
-__host__ __device__ constexpr int slot_H(int mode, int c)
-{
-    return mode == 0 ? (c < 2 ? 1 + c : -1) : (mode == 1 ? (c == 2 ? 2 : -1) : 3 + c);
-}
-
 // acc += w e^{j phi} (J, M) of one face cell with outward normal sgn * e_AX,
 // J = n x H, M = -n x E; (e_AX x V)_b1 = -V_b2, (e_AX x V)_b2 = V_b1.
 template <int MODE, int AX>

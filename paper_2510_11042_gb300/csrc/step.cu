@@ -52,32 +52,6 @@
 namespace lbem {
 namespace {
 
-// x/3 to within rounding: the constant 1/3 split into a float and a remainder,
-// x*hi + x*lo evaluated with one rounding (FMA).  A plain x * fl(1/3) is biased
-// upwards (fl(1/3) > 1/3), which would make the collision grow D and B by
-// ~2e-8 per step; this form is unbiased.
-__device__ __forceinline__ float third(float x)
-{
-    constexpr float hi = 0.333333343267f;        // fl(1/3)
-    constexpr float lo = -9.934107481e-09f;      // 1/3 - fl(1/3)
-    return fmaf(x, hi, x * lo);
-}
-
-// Direction i = 0..6: rest, +x, -x, +y, -y, +z, -z.
-__host__ __device__ constexpr int dir_axis(int i) { return i == 0 ? -1 : (i - 1) / 2; }
-__host__ __device__ constexpr int dir_sign(int i) { return i == 0 ? 0 : ((i & 1) ? 1 : -1); }
-
-// (c_i x V)_a for an axis-aligned unit velocity c_i.
-__device__ __forceinline__ float cross_c(int i, const float V[3], int a)
-{
-    const int d = dir_axis(i);
-    const float s = (float)dir_sign(i);
-    // e_x x V = (0, -Vz, Vy), e_y x V = (Vz, 0, -Vx), e_z x V = (-Vy, Vx, 0)
-    if (d == 0) return a == 0 ? 0.f : (a == 1 ? -s * V[2] : s * V[1]);
-    if (d == 1) return a == 0 ? s * V[2] : (a == 1 ? 0.f : -s * V[0]);
-    return a == 0 ? -s * V[1] : (a == 1 ? s * V[0] : 0.f);
-}
-
 template <int MODE>
 __device__ __forceinline__ void moments(const float *f, float inv_eps, float D[3], float E[3],
                                         float H[3])
@@ -120,18 +94,6 @@ __device__ __forceinline__ void collide(float *f, const float D[3], const float 
             eq2 = (i == 0) ? 0.f : H3[a] + cross_c(i, E3, a);
         f[q] = eq2 - f[q];
     }
-}
-
-__device__ __forceinline__ float layer_keep(int d, int w, float sigma_max, float inv_w)
-{
-    if (d >= w) return 1.f;
-    const float m = (float)(w - d) * inv_w;
-    return 1.f - sigma_max * m * m * m;
-}
-
-__device__ __forceinline__ bool in_box(int x, int y, int z, const int lo[3], const int hi[3])
-{
-    return x >= lo[0] && x <= hi[0] && y >= lo[1] && y <= hi[1] && z >= lo[2] && z <= hi[2];
 }
 
 // One node s of the incident line: line_out[.][s] = update of line_in at node s
@@ -213,7 +175,7 @@ struct FloatCell {
 // Values are in storage units (population / scale); fields go to the DFT
 // multiplied back by the scale (dft_scale_cells), the incident source is
 // divided by it.
-template <int MODE, class Cell>
+template <int MODE, bool REC = false, class Cell>
 __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float inv_eps,
                                             const StepArgs &a)
 {
@@ -225,6 +187,21 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
     for (int q = 0; q < Q; ++q) {
         if (PL::fam(q) == 0) D[PL::comp(q)] += f.get(q);
         else B[PL::comp(q)] += f.get(q);
+    }
+    if (REC) {
+        // total-field D of this step's pulled populations, for the adjoint's
+        // permittivity derivative
+        float Dinc[3] = {0.f, 0.f, 0.f};
+        if (a.tfsf && in_box(x, y, z, a.tf_lo, a.tf_hi)) {
+            const int sl = a.inc_axis == 0 ? x : (a.inc_axis == 1 ? y : z);
+#pragma unroll
+            for (int q = 0; q < 7 * PL::NE; ++q)
+                Dinc[PL::comp(q)] += __ldg(a.line_n1 + (size_t)q * a.n_line + sl);
+        }
+        const long long c = ((long long)z * a.ny + y) * a.nxp + x;
+#pragma unroll
+        for (int k = 0; k < PL::NE; ++k)
+            a.rec[(long long)k * a.P + c] = D[M::ec(k)] * a.scale + Dinc[M::ec(k)];
     }
     float E[3], E3[3] = {0.f, 0.f, 0.f}, H3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -339,7 +316,7 @@ template <> __device__ __forceinline__ void store_pop<__nv_bfloat16>(__nv_bfloat
 // loads shifted by one element (coalesced; the extra sector per warp hits in
 // L1/L2).
 // The cells x = bx * BX + threadIdx.x of row (y, z) for one step.
-template <int MODE, class S, int BX>
+template <int MODE, class S, int BX, bool REC = false>
 __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int z)
 {
     using PL = Planes<MODE>;
@@ -362,12 +339,12 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
 #pragma unroll
     for (int q = 0; q < Q; ++q) f[q] = load_pop<S>(static_cast<const S *>(a.fin_q[q]) + src[PL::dir(q)]);
     FloatCell cell{f};
-    update_cell<MODE>(cell, x, y, z, __ldg(a.inv_eps + c), a);
+    update_cell<MODE, REC>(cell, x, y, z, __ldg(a.inv_eps + c), a);
 #pragma unroll
     for (int q = 0; q < Q; ++q) store_pop<S>(static_cast<S *>(a.fout_q[q]) + c, f[q]);
 }
 
-template <int MODE, class S, int BX>
+template <int MODE, class S, int BX, bool REC = false>
 __global__ void __launch_bounds__(BX, sizeof(S) == 4 ? 6 : 7) step_kernel_cell(const StepArgs a)
 {
     const int b = blockIdx.x;
@@ -377,7 +354,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 4 ? 6 : 7) step_kernel_cell(c
     }
     int bx, y, z;
     block_row(a, b, bx, y, z);
-    row_cells<MODE, S, BX>(a, bx, y, z);
+    row_cells<MODE, S, BX, REC>(a, bx, y, z);
 }
 
 constexpr int kBX = 128;  // threads per block = cells per row tile
@@ -525,13 +502,14 @@ __global__ void line_init_kernel(const StepArgs a)
 }
 
 
-template <int MODE, class S>
+template <int MODE, class S, bool REC = false>
 cudaError_t launch_cell(StepArgs a, cudaStream_t s)
 {
     a.nblk_x = (a.nx + kBX - 1) / kBX;
     a.nblk_main = a.nblk_x * a.ny * a.nz;
     if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
-    step_kernel_cell<MODE, S, kBX><<<a.nblk_main, kBX, 0, s>>>(a);
+    if (REC && a.rec == nullptr) return cudaErrorInvalidValue;
+    step_kernel_cell<MODE, S, kBX, REC><<<a.nblk_main, kBX, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -596,6 +574,16 @@ cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s
     case 6: return launch_cell<2, float>(a, s);
     case 7: return launch_cell<2, __half>(a, s);
     case 8: return launch_cell<2, __nv_bfloat16>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step_record(int mode, const StepArgs &a, cudaStream_t s)
+{
+    switch (mode) {
+    case 0: return launch_cell<0, float, true>(a, s);
+    case 1: return launch_cell<1, float, true>(a, s);
+    case 2: return launch_cell<2, float, true>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -93,6 +93,9 @@ _SIGS = {
     "lbem_batch_launches": (_I64, [_P]),
     "lbem_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbem_batch_destroy": (None, [_P]),
+    "lbem_adjoint_workspace_bytes": (_I32, [_P, _I64, _I32, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbem_forward_checkpointed": (_I32, [_P, _I64, _I32, _P, ctypes.c_size_t]),
+    "lbem_adjoint": (_I32, [_P, _P, _P, _P, _I32, _P, _I32, ctypes.POINTER(ctypes.c_double)]),
     "lbem_sync": (_I32, [_P]),
     "lbem_destroy": (None, [_P]),
     "lbem_last_error": (ctypes.c_char_p, [_P]),
@@ -376,6 +379,33 @@ class Batch:
             pass
 
 
+def lbem_adjoint_workspace_bytes(h, n_steps: int, K: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().lbem_adjoint_workspace_bytes(h, int(n_steps), int(K), ctypes.byref(n)), h)
+    return n.value
+
+
+def lbem_forward_checkpointed(h, n_steps: int, K: int, workspace=None):
+    """workspace: torch uint8 CUDA tensor of lbem_adjoint_workspace_bytes() or None."""
+    wp, _ = _ptr(workspace)
+    wbytes = workspace.numel() if workspace is not None else 0
+    _check(lib().lbem_forward_checkpointed(h, int(n_steps), int(K), wp, wbytes), h)
+
+
+def lbem_adjoint(h, theta, phi, weights, grad_out) -> float:
+    """grad_out: float32 [nz][ny][nx] numpy array or torch CUDA tensor.  Returns J."""
+    theta = np.ascontiguousarray(theta, np.float64)
+    phi_a = None if phi is None else np.ascontiguousarray(phi, np.float64)
+    w = np.ascontiguousarray(weights, np.float64)
+    if w.size != theta.size or (phi_a is not None and phi_a.size != theta.size):
+        raise ValueError("theta, phi and weights must have the same length")
+    gp, on_dev = _ptr(grad_out)
+    J = ctypes.c_double()
+    _check(lib().lbem_adjoint(h, theta.ctypes.data, None if phi_a is None else phi_a.ctypes.data,
+                              w.ctypes.data, theta.size, gp, on_dev, ctypes.byref(J)), h)
+    return J.value
+
+
 def lbem_sync(h):
     _check(lib().lbem_sync(h), h)
 
@@ -443,6 +473,10 @@ class Solver:
         self.wave = wave
         lbem_inject_plane_wave(self.h, plane_wave_desc(wave))
 
+    def set_permittivity(self, eps):
+        lbem_set_permittivity(self.h, eps if hasattr(eps, "data_ptr") else
+                              np.ascontiguousarray(eps, np.float32))
+
     def set_dft_window(self, t_start, n_periods=1):
         lbem_set_dft_window(self.h, t_start, n_periods)
 
@@ -481,6 +515,25 @@ class Solver:
 
     def sync(self):
         lbem_sync(self.h)
+
+    def forward_checkpointed(self, n_steps, K):
+        """Take n_steps steps from t = 0 keeping every K-th state for lbem_adjoint."""
+        torch = self.torch
+        with torch.cuda.device(self.device):
+            nbytes = lbem_adjoint_workspace_bytes(self.h, n_steps, K)
+            self.adj_workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            lbem_forward_checkpointed(self.h, n_steps, K, self.adj_workspace)
+
+    def adjoint(self, theta, phi=None, weights=None):
+        """(J, dJ/deps_r) for J = sum_k weights_k |S(theta_k, phi_k)|^2; the
+        gradient is a float32 CUDA tensor [nz][ny][nx]."""
+        torch = self.torch
+        theta = np.atleast_1d(np.asarray(theta, np.float64))
+        w = np.ones_like(theta) if weights is None else np.atleast_1d(np.asarray(weights, np.float64))
+        nx, ny, nz = self.shape
+        g = torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
+        J = lbem_adjoint(self.h, theta, phi, w, g)
+        return J, g
 
     def kernel_launches(self):
         return lbem_kernel_launches(self.h)

@@ -1,0 +1,203 @@
+"""GPU adjoint (lbem_forward_checkpointed / lbem_adjoint and the autograd
+binding) against the FP64 oracle: element-wise against the oracle's own
+discrete-adjoint gradient on small grids, and against central finite
+differences of FP64 oracle forward runs on sampled design cells of the
+512 x 512 hexagon workload (4000 steps, checkpoints every 200 steps).
+
+Tolerances.  The GPU runs the same linear recurrences as the oracle in FP32;
+the FP32 forward matches the oracle to ~1e-6 relative, and the gradient is
+a sum over all steps of products of adjoint and forward fields whose terms
+largely cancel, so its error relative to the largest gradient entry is
+allowed 2e-4 (relative L2 over the grid 2e-4); J itself must meet the
+forward far-field bar, 1e-5.
+"""
+import dataclasses
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from _parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+J_TOL = 1e-5
+G_TOL = 2e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_11042_gb300 import lbem
+    lbem.lib()
+
+
+def small_problem(mode):
+    """A scatterer plus a seeded random design region, long enough for the
+    scattered wave to fill the NTFF box.  2D: 144 x 48 (two 128-cell row tiles,
+    the second ragged); 3D: 24 x 24 x 40 (incidence along z)."""
+    rng = np.random.default_rng(11)
+    if mode == "3d":
+        shape, lam, w, periods = (24, 24, 40), 4.0, 4, 10
+    else:
+        shape, lam, w, periods = (144, 48, 1), 6.0, 6, 25
+    nx, ny, nz = shape
+    wave = W.axis_wave(mode, shape, w, lam, gap_ntff=2, gap_tf=2)
+    eps = np.ones((nz, ny, nx), np.float32)
+    lo, hi = wave.tf_lo, wave.tf_hi
+    if mode == "3d":
+        eps[18:24, 9:15, 9:15] = 2.25
+        eps[14:28, 8:16, 8:16] *= rng.uniform(1.0, 1.3, (14, 8, 8)).astype(np.float32)
+    else:
+        y, x = np.mgrid[0:ny, 0:nx]
+        eps[0][(x - 40) ** 2 + (y - 23.5) ** 2 <= 16] = 2.25
+        eps[0, 14:34, 30:60] *= rng.uniform(1.0, 1.3, (20, 30)).astype(np.float32)
+    T = int(round(3 * lam))
+    return W.Problem(name=f"adjoint_small_{mode}", mode=mode, shape=shape, eps=eps,
+                     absorber_width=w, sigma_max=W.DEFAULT_SIGMA_MAX, wave=wave,
+                     steps=periods * T, dft_periods=1)
+
+
+def angles_of(mode):
+    if mode == "3d":
+        return (np.array([0.0, math.pi / 4, math.pi / 2]), np.array([0.0, 0.0, math.pi / 2]),
+                np.array([1.0, 0.5, 0.25]))
+    return np.array([0.0, math.pi / 4, math.pi / 2]), None, np.array([1.0, 0.5, 0.25])
+
+
+def gpu_gradient(problem, theta, phi, w, K):
+    from paper_2510_11042_gb300 import lbem
+    s = lbem.Solver(problem.shape, problem.eps, problem.mode, "f32", problem.absorber_width,
+                    problem.sigma_max)
+    s.inject(problem.wave)
+    s.set_dft_window(problem.dft_start, problem.dft_periods)
+    s.forward_checkpointed(problem.steps, K)
+    J, g = s.adjoint(theta, phi, w)
+    return J, g.cpu().numpy().astype(np.float64), s
+
+
+def oracle_problem(problem):
+    return dataclasses.replace(problem, eps=np.asarray(problem.eps, np.float64))
+
+
+@pytest.mark.parametrize("mode", ["ez", "hz", "3d"])
+def test_gradient_matches_oracle_adjoint(mode):
+    from oracle import adjoint
+    p = small_problem(mode)
+    theta, phi, w = angles_of(mode)
+    K = 64 if mode != "3d" else 16            # several segments and a short last one
+    assert p.steps % K != 0
+    J, g, s = gpu_gradient(p, theta, phi, w, K)
+    angles = list(zip(theta, phi if phi is not None else np.zeros_like(theta)))
+    Jo, go, _ = adjoint.gradient(oracle_problem(p), angles, w)
+    assert Jo > 0 and np.max(np.abs(go)) > 0
+    assert abs(J - Jo) <= J_TOL * Jo, (J, Jo)
+    err = rel_l2(g, go)
+    emax = np.max(np.abs(g - go)) / np.max(np.abs(go))
+    print(f"{mode}: J {J:.9g} vs {Jo:.9g}; gradient rel L2 {err:.2e}, max/max {emax:.2e}")
+    assert err <= G_TOL and emax <= G_TOL
+    # the design of the checkpointing does not change the result
+    J2, g2, _ = gpu_gradient(p, theta, phi, w, p.steps)
+    assert J2 == J
+    assert np.max(np.abs(g2 - g)) <= 1e-6 * np.max(np.abs(g))
+
+
+def test_autograd_function_matches_solver():
+    import torch
+    from paper_2510_11042_gb300.autograd import far_field_intensity
+    p = small_problem("ez")
+    theta, phi, w = angles_of("ez")
+    eps = torch.tensor(p.eps, device="cuda", requires_grad=True)
+    s2 = far_field_intensity(eps, p, theta, None, K=30)
+    loss = (s2 * torch.tensor(w, dtype=torch.float64, device="cuda")).sum()
+    loss.backward()
+    J, g, _ = gpu_gradient(p, theta, None, w, 30)
+    assert loss.item() == pytest.approx(J, rel=1e-12)
+    assert torch.equal(eps.grad.cpu(), torch.tensor(g, dtype=torch.float32))
+
+
+def test_adjoint_state_errors():
+    from paper_2510_11042_gb300 import lbem
+    p = small_problem("ez")
+    s = lbem.Solver(p.shape, p.eps, "ez", "f32", p.absorber_width, p.sigma_max)
+    s.inject(p.wave)
+    s.set_dft_window(p.dft_start, p.dft_periods)
+    with pytest.raises(lbem.LbemError) as e:
+        s.adjoint([0.0])
+    assert e.value.code == lbem.LBEM_ERR_STATE
+    s.forward_checkpointed(p.steps, 40)
+    J, _ = s.adjoint([0.0])
+    assert J > 0
+    with pytest.raises(lbem.LbemError) as e:              # not from t = 0
+        s.forward_checkpointed(10, 5)
+    assert e.value.code == lbem.LBEM_ERR_STATE
+    s.set_permittivity(p.eps)                             # discards the checkpoints
+    with pytest.raises(lbem.LbemError) as e:
+        s.adjoint([0.0])
+    assert e.value.code == lbem.LBEM_ERR_STATE
+    s.close()
+    # a window that ends after the checkpointed run
+    s = lbem.Solver(p.shape, p.eps, "ez", "f32", p.absorber_width, p.sigma_max)
+    s.inject(p.wave)
+    s.set_dft_window(p.dft_start, p.dft_periods)
+    s.forward_checkpointed(p.steps - 5, 40)
+    with pytest.raises(lbem.LbemError) as e:
+        s.adjoint([0.0])
+    assert e.value.code == lbem.LBEM_ERR_STATE
+    s.close()
+    h = lbem.Solver(p.shape, p.eps, "ez", "f16", p.absorber_width, p.sigma_max)
+    h.inject(p.wave)
+    with pytest.raises(lbem.LbemError) as e:
+        h.forward_checkpointed(10, 5)
+    assert e.value.code == lbem.LBEM_ERR_ARG
+    h.close()
+
+
+def test_hexagon_gradient_vs_finite_differences():
+    """512 x 512 hexagon, 4000 steps, K = 200: dJ/deps_r of |S(theta)|^2 at 0, 45
+    and 90 degrees against central differences (h = 1e-4 eps_r) of FP64
+    oracle runs on seeded design cells (LBEM_FD_CELLS, default 2)."""
+    from oracle import lb, ntff
+    p = W.adjoint_problem()
+    theta = np.array(p.meta["angles"])
+    from paper_2510_11042_gb300 import lbem
+    s = lbem.Solver(p.shape, p.eps, "ez", "f32", p.absorber_width, p.sigma_max)
+    s.inject(p.wave)
+    s.set_dft_window(p.dft_start, p.dft_periods)
+    s.forward_checkpointed(p.steps, 200)
+    grads = []
+    for k in range(3):
+        wk = np.zeros(3)
+        wk[k] = 1.0
+        J, g = s.adjoint(theta, None, wk)
+        grads.append((J, g.cpu().numpy().astype(np.float64)))
+    ncells = int(os.environ.get("LBEM_FD_CELLS", "2"))
+    rng = np.random.default_rng(7)
+    c0, d = p.meta["design_lo"], p.meta["design"]
+    cells = [(0, int(c0 + rng.integers(d)), int(c0 + rng.integers(d))) for _ in range(ncells)]
+    k = 2 * math.pi / p.wave.wavelength
+
+    def s2_oracle(eps):
+        r = lb.Run(dataclasses.replace(p, eps=eps)).run()
+        return ntff.far_field(r.phasors(), p.wave.ntff_lo, p.wave.ntff_hi, k, p.wave.center,
+                              r.incident_amplitude(), "ez", theta)
+
+    base = np.asarray(p.eps, np.float64)
+    s2o = s2_oracle(base)
+    for kk in range(3):
+        assert abs(grads[kk][0] - s2o[kk]) <= J_TOL * s2o[kk], (kk, grads[kk][0], s2o[kk])
+    for cell in cells:
+        h = 1e-4 * base[cell]
+        ep = base.copy(); ep[cell] += h
+        em = base.copy(); em[cell] -= h
+        fd = (s2_oracle(ep) - s2_oracle(em)) / (2 * h)
+        for kk in range(3):
+            g = grads[kk][1]
+            gmax = np.max(np.abs(g))
+            print(f"cell {cell} theta {math.degrees(theta[kk]):.0f}: adjoint {g[cell]:.6e} "
+                  f"fd {fd[kk]:.6e} (max |g| {gmax:.3e})")
+            assert abs(g[cell] - fd[kk]) <= G_TOL * gmax + 1e-3 * abs(fd[kk])

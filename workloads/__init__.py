@@ -213,6 +213,26 @@ def hexagon_problem(n=512, side=60.0, eps_in=2.25, wavelength=40.0, w=20, steps=
                    meta=dict(side=side, eps_in=eps_in))
 
 
+def adjoint_problem(n=512, side=60.0, design=128, seed=7, wavelength=40.0, w=20, steps=4000,
+                    mode="ez") -> Problem:
+    """Permittivity-gradient workload: the hexagon of hexagon_problem with the
+    central design x design cells as design variables; design cells inside the
+    hexagon get eps_r = 2.25 (1 + u), u ~ U[-0.05, 0.05] (seeded), the others
+    stay 1.  Objectives |S(theta)|^2 at theta = 0, 45 and 90 degrees."""
+    p = hexagon_problem(n=n, side=side, eps_in=2.25, wavelength=wavelength, w=w, steps=steps,
+                        mode=mode)
+    eps = p.eps.copy()
+    c0 = (n - design) // 2
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-0.05, 0.05, size=(design, design))
+    region = eps[0, c0:c0 + design, c0:c0 + design]
+    inside = region > 1.0
+    region[inside] = (2.25 * (1.0 + u[inside])).astype(np.float32)
+    return replace(p, name=f"adjoint_hexagon_{mode}_{n}", eps=eps,
+                   meta=dict(p.meta, design_lo=c0, design=design,
+                             angles=(0.0, math.pi / 4, math.pi / 2)))
+
+
 def batched_problems(count=32, seed=20251011, w=16):
     """Uneven batch of cylinders: N = 32*ceil(U{256..1024}/32), eps ~ U[1.5, 6],
     x ~ U[1, 10], lambda ~ U{24..48}; resampled until 2a + 2(W + 12) <= N."""
