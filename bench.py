@@ -254,6 +254,7 @@ def run_gpu(args, rank, world, local_rank):
     K, Wm = args.steps, args.warmup
     main = one_storage("f32", K, Wm, True)
     batched = None if (args.no_batch or world > 1) else run_batched(dev)
+    adjoint = None if (args.no_adjoint or world > 1) else run_adjoint(dev)
     secondary = {}
     if not args.fp32_only:
         for st in ("f16", "bf16"):
@@ -320,6 +321,8 @@ def run_gpu(args, rank, world, local_rank):
     }
     if batched:
         line["batched"] = batched
+    if adjoint:
+        line["adjoint"] = adjoint
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.size, budget_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -404,6 +407,64 @@ def _batch_vs_sequential(dev, probs):
             "sequential_mlups": round(work / t_seq / 1e6, 1),
             "speedup": round(t_seq / t_batch, 3),
             "autotuned": {"blocks_per_sm": bps, "rows_per_item": rpi}}
+
+
+# ------------------------------------------------------------------ adjoint workload
+def run_adjoint(dev, K=200):
+    """Permittivity gradient of |S(theta)|^2 at theta = 0, 45, 90 degrees on the
+    512 x 512 hexagon design workload (EZ, 4000 steps, design 128 x 128):
+    one checkpointed forward run, then one adjoint run per objective.  The
+    adjoint step kernel's bandwidth is its algorithmic bytes per cell (mu in
+    and out, 1/eps_r, the recorded D, the FP64 gradient read and written) over
+    its CUDA-event time; the 512^2 working set (~100 MB) fits in L2."""
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    p = W.adjoint_problem()
+    nx, ny, nz = p.shape
+    cells = nx * ny * nz
+    theta = np.array(p.meta["angles"])
+    s = lbem.Solver(p.shape, p.eps, p.mode, "f32", p.absorber_width, p.sigma_max, device=dev)
+    s.inject(p.wave)
+    s.set_dft_window(p.dft_start, p.dft_periods)
+    l0 = s.kernel_launches()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s.forward_checkpointed(p.steps, K)
+    torch.cuda.synchronize(dev)
+    t_fwd = time.perf_counter() - t0
+    runs = []
+    for k in range(3):
+        wk = np.zeros(3)
+        wk[k] = 1.0
+        t0 = time.perf_counter()
+        J, g = s.adjoint(theta, None, wk)
+        torch.cuda.synchronize(dev)
+        runs.append((time.perf_counter() - t0, J, lbem.lbem_adjoint_timing(s.h),
+                     float(g.abs().max().item())))
+    launches = s.kernel_launches() - l0
+    s.close()
+    torch.cuda.empty_cache()
+    hbm, _ = peaks()
+    q, ne = 21, 1
+    bytes_adj = 2 * q * 4 + 4 + 4 * ne + 16
+    back_ms = statistics.median(r[2][1] for r in runs)
+    replay_ms = statistics.median(r[2][0] for r in runs)
+    t_adj = statistics.median(r[0] for r in runs)
+    ach = bytes_adj * cells * p.steps / (back_ms / 1e3) / 1e9
+    return {"workload": f"hexagon {nx}x{ny} EZ, side 60, design 128x128 (seed 7), lambda 40, "
+                        f"W 20, {p.steps} steps, checkpoint every {K}, FP32",
+            "objectives": "|S(theta)|^2 at 0, 45, 90 deg, one adjoint run each",
+            "forward_checkpointed_s": round(t_fwd, 4),
+            "adjoint_s_per_objective": round(t_adj, 4),
+            "adjoint_over_forward": round(t_adj / t_fwd, 3),
+            "replay_ms": round(replay_ms, 3), "backward_ms": round(back_ms, 3),
+            "gradient_mlups": round(cells * p.steps / t_adj / 1e6, 1),
+            "J": [r[1] for r in runs], "max_abs_grad": [round(r[3], 6) for r in runs],
+            "gpu_launches": int(launches),
+            "adjoint_step_roofline": {"bound": "hbm", "bytes_per_cell": bytes_adj,
+                                      "achieved": round(ach, 1), "peak": hbm,
+                                      "unit": "GB/s", "frac": round(ach / hbm, 4),
+                                      "note": "working set L2-resident at 512^2"}}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -500,6 +561,7 @@ def main():
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-updates", type=float, default=2)
     args = ap.parse_args()

@@ -267,6 +267,9 @@ int32_t lbem_forward_checkpointed(lbem_handle h, int64_t n_steps, int32_t K, voi
 int32_t lbem_adjoint(lbem_handle h, const double *theta_host, const double *phi_host,
                      const double *weights_host, int32_t n_ang, float *grad_out,
                      int32_t grad_on_device, double *J_out);
+/* Device time (CUDA events on the handle's stream) of the last lbem_adjoint
+ * call: the forward replays of all segments and the adjoint steps. */
+int32_t lbem_adjoint_timing(lbem_handle h, double *replay_ms, double *backward_ms);
 
 /* Far-field projection that allocates nothing (the paper has no counterpart;
  * this is a library convenience).  For callers that cannot call cudaMalloc or

@@ -58,6 +58,7 @@ struct lbem_ctx {
     bool adj_valid = false;
     int64_t adj_steps = 0;
     int adj_K = 0;
+    double adj_replay_ms = 0.0, adj_backward_ms = 0.0;  // of the last lbem_adjoint
     char err[512];
 };
 
@@ -543,6 +544,7 @@ struct lbem_batch_ctx {
     bool adj_valid = false;
     int64_t adj_steps = 0;
     int adj_K = 0;
+    double adj_replay_ms = 0.0, adj_backward_ms = 0.0;  // of the last lbem_adjoint
     char err[512];
 };
 
@@ -1284,8 +1286,16 @@ int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, cons
     }
     b.dft_scale = scale;
 
+    // phase timing: events before the replay, between replay and backward, after
+    std::vector<cudaEvent_t> ev((size_t)3 * L.nseg, nullptr);
+    struct EventGuard {
+        std::vector<cudaEvent_t> &v;
+        ~EventGuard() { for (cudaEvent_t e : v) if (e) cudaEventDestroy(e); }
+    } guard{ev};
+    for (auto &e : ev) CK(h, cudaEventCreate(&e));
     for (int seg = L.nseg - 1; seg >= 0; --seg) {
         const int64_t t0 = (int64_t)seg * h->adj_K;
+        CK(h, cudaEventRecord(ev[3 * seg], h->stream));
         const int64_t len = std::min<int64_t>(h->adj_K, h->adj_steps - t0);
         const char *ck = W + L.ck0 + (size_t)seg * L.ck_stride;
         CK(h, cudaMemcpyAsync(rf[0], ck, pop, cudaMemcpyDeviceToDevice, h->stream));
@@ -1307,6 +1317,7 @@ int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, cons
             if (e != cudaSuccess) return cuda_fail(h, e, "replay step launch");
             h->launches += 1;
         }
+        CK(h, cudaEventRecord(ev[3 * seg + 1], h->stream));
         for (int64_t k = len - 1; k >= 0; --k) {
             const int64_t tf = t0 + k + 1;   // time of the fields of this step
             for (int q = 0; q < h->Q; ++q) {
@@ -1325,6 +1336,7 @@ int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, cons
             h->launches += 1;
             mcur ^= 1;
         }
+        CK(h, cudaEventRecord(ev[3 * seg + 2], h->stream));
     }
 
     // 4. dJ/deps_r and J
@@ -1336,12 +1348,28 @@ int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, cons
     std::vector<double> s2(n_ang);
     CK(h, cudaMemcpyAsync(s2.data(), d_s2, n_ang * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    h->adj_replay_ms = h->adj_backward_ms = 0.0;
+    for (int seg = 0; seg < L.nseg; ++seg) {
+        float r = 0.f, b2 = 0.f;
+        CK(h, cudaEventElapsedTime(&r, ev[3 * seg], ev[3 * seg + 1]));
+        CK(h, cudaEventElapsedTime(&b2, ev[3 * seg + 1], ev[3 * seg + 2]));
+        h->adj_replay_ms += r;
+        h->adj_backward_ms += b2;
+    }
     if (J_out) {
         double J = 0.0;
         for (int i = 0; i < n_ang; ++i) J += weights[i] * s2[i];
         *J_out = J;
     }
     return check_status(h);
+}
+
+int32_t lbem_adjoint_timing(lbem_handle h, double *replay_ms, double *backward_ms)
+{
+    if (!h || !replay_ms || !backward_ms) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    *replay_ms = h->adj_replay_ms;
+    *backward_ms = h->adj_backward_ms;
+    return LBEM_OK;
 }
 
 const char *lbem_last_error(lbem_handle h) { return h ? h->err : g_create_err; }

@@ -96,6 +96,7 @@ _SIGS = {
     "lbem_adjoint_workspace_bytes": (_I32, [_P, _I64, _I32, ctypes.POINTER(ctypes.c_size_t)]),
     "lbem_forward_checkpointed": (_I32, [_P, _I64, _I32, _P, ctypes.c_size_t]),
     "lbem_adjoint": (_I32, [_P, _P, _P, _P, _I32, _P, _I32, ctypes.POINTER(ctypes.c_double)]),
+    "lbem_adjoint_timing": (_I32, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "lbem_sync": (_I32, [_P]),
     "lbem_destroy": (None, [_P]),
     "lbem_last_error": (ctypes.c_char_p, [_P]),
@@ -404,6 +405,13 @@ def lbem_adjoint(h, theta, phi, weights, grad_out) -> float:
     _check(lib().lbem_adjoint(h, theta.ctypes.data, None if phi_a is None else phi_a.ctypes.data,
                               w.ctypes.data, theta.size, gp, on_dev, ctypes.byref(J)), h)
     return J.value
+
+
+def lbem_adjoint_timing(h):
+    """(replay_ms, backward_ms) of the last lbem_adjoint call."""
+    r, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lbem_adjoint_timing(h, ctypes.byref(r), ctypes.byref(b)), h)
+    return r.value, b.value
 
 
 def lbem_sync(h):
