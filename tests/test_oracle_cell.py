@@ -171,3 +171,34 @@ def test_vacuum_stays_zero_and_sponge_profile():
     # corners take the larger of the two faces; z of a 2D grid is not a face
     assert lb.sigma((0, 5, 0), gn, 10, 0.3) == pytest.approx(0.3)
     assert lb.sigma((20, 20, 0), gn, 10, 0.3) == 0.0
+
+
+def test_energy_of_equilibrium_cells_is_the_field_energy():
+    """orc_energy sums 1/2 (eps |E|^2 + mu |H|^2) over the box: for cells holding
+    the equilibrium of given fields the result is that closed form."""
+    rng = np.random.default_rng(5)
+    shape = (3, 2, 2)
+    eps = rng.uniform(1.0, 4.0, shape[::-1])
+    mu = rng.uniform(1.0, 3.0, shape[::-1])
+    lat = lb.Lattice(shape, eps, mu=mu)
+    E = rng.standard_normal((lat.ncell, 3))
+    H = rng.standard_normal((lat.ncell, 3))
+    e, m = eps.reshape(-1), mu.reshape(-1)
+    for c in range(lat.ncell):
+        lat.f[c] = lb.equilibrium(E[c], H[c], e[c], m[c])
+    want = 0.5 * np.sum(e[:, None] * E ** 2 + m[:, None] * H ** 2)
+    assert lat.energy() == pytest.approx(want, rel=1e-13)
+
+
+def test_error_metrics_of_eqs_12_13_closed_forms():
+    from oracle import metrics
+    ref = np.array([1.0, 4.0, 2.0, 0.5])
+    assert metrics.normalized_rms(ref, ref) == 0.0
+    # a constant offset d gives |d| / max(ref) for both metrics
+    d = 0.2
+    assert metrics.normalized_rms(ref + d, ref) == pytest.approx(d / 4.0, rel=1e-15)
+    assert np.allclose(metrics.normalized_abs_error(ref - d, ref), d / 4.0, rtol=1e-15)
+    # RMS of a single error e among n samples: |e| / sqrt(n) / max(ref)
+    s = ref.copy()
+    s[2] += 0.8
+    assert metrics.normalized_rms(s, ref) == pytest.approx(0.8 / 2.0 / 4.0, rel=1e-15)
