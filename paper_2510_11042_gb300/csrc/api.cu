@@ -443,7 +443,7 @@ int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
         return fail(h, LBEM_ERR_ARG, "source_index must lie upstream of the total-field box");
     if (h->has_wave) {
         // the stored state holds scattered parts inside the old box: make it total again
-        CK(h, launch_add_incident(h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx, h->g.ny,
+        CK(h, launch_add_incident(h->g.mode, h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx, h->g.ny,
                                   h->g.nz, h->nxp, inc_view(h), 1.0f, h->stream));
         h->launches += 1;
         CK(h, cudaStreamSynchronize(h->stream));
@@ -870,7 +870,7 @@ int32_t lbem_get_populations(lbem_handle h, float *out, int32_t on_device)
     if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
     for (int q = 0; q < h->Q; ++q) {
         float *dst = on_device ? out + (size_t)q * h->ncell : h->stage;
-        CK(h, launch_pack(h->g.storage, h->f[h->cur], h->P, q, h->scale, dst, h->g.nx, h->g.ny,
+        CK(h, launch_pack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, h->scale, dst, h->g.nx, h->g.ny,
                           h->g.nz, h->nxp, inc_view(h), h->stream));
         h->launches += 1;
         if (!on_device)
@@ -891,7 +891,7 @@ int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t on_device)
             CK(h, cudaMemcpyAsync(h->stage, src, (size_t)h->ncell * 4, cudaMemcpyHostToDevice, h->stream));
             src = h->stage;
         }
-        CK(h, launch_unpack(h->g.storage, h->f[h->cur], h->P, q, h->inv_scale, src, h->g.nx,
+        CK(h, launch_unpack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, h->inv_scale, src, h->g.nx,
                             h->g.ny, h->g.nz, h->nxp, inc_view(h), h->stream));
         h->launches += 1;
         if (!on_device) CK(h, cudaStreamSynchronize(h->stream));  // stage is reused
@@ -1039,9 +1039,9 @@ int32_t lbem_set_storage_scale(lbem_handle h, float scale)
         IncView none;
         std::memset(&none, 0, sizeof none);
         for (int q = 0; q < h->Q; ++q) {
-            CK(h, launch_pack(h->g.storage, h->f[h->cur], h->P, q, ratio, h->stage, h->g.nx, h->g.ny,
+            CK(h, launch_pack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, ratio, h->stage, h->g.nx, h->g.ny,
                               h->g.nz, h->nxp, none, h->stream));
-            CK(h, launch_unpack(h->g.storage, h->f[h->cur], h->P, q, 1.0f, h->stage, h->g.nx, h->g.ny,
+            CK(h, launch_unpack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, 1.0f, h->stage, h->g.nx, h->g.ny,
                                 h->g.nz, h->nxp, none, h->stream));
             h->launches += 2;
         }

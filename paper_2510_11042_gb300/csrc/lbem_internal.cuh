@@ -51,6 +51,54 @@ template <int MODE> struct Planes {
 inline int planes_of_mode(int mode) { return mode == 2 ? 42 : 21; }
 inline int dft_comps_of_mode(int mode) { return mode == 2 ? 6 : 3; }
 
+// ------------------------------------------------ population storage layout
+// The populations of one buffer are grouped by direction.  Direction i holds
+// the NC = NE + NH scalars of that direction in slots s = 0..NC-1 (the mode's
+// e components, then its h components) in a block of NC*P elements starting
+// at element i*NC*P (P: plane stride, cells padded in x).  The block is split
+// into groups of consecutive slots; a group of width W whose first slot is s0
+// starts at element (i*NC + s0)*P and keeps cell c's slot s at
+// (i*NC + s0)*P + W*c + (s - s0), so one vector access fetches a whole group
+// of a cell (all of a group's slots stream along the same velocity c_i):
+//   3D FP32:  {e_x e_y} {e_z h_x} {h_y h_z}   three 8-byte pairs
+//   3D 16-bit: {e_x e_y e_z h_x} {h_y h_z}    one 8-byte quad and one 4-byte pair
+//   2D (both): {s0 s1} {s2}                   a pair and a single
+// The buffer size is Q*P elements as for plain planes, and the start of plane
+// slot q' = i*NC + s0 (q'*P elements) is where a group begins.
+__host__ __device__ constexpr int mode_NE(int mode) { return mode == 0 ? 1 : (mode == 1 ? 2 : 3); }
+__host__ __device__ constexpr int mode_NH(int mode) { return mode == 0 ? 2 : (mode == 1 ? 1 : 3); }
+// population plane q (e-planes q = i*NE + k, then h-planes 7*NE + i*NH + k) -> direction / slot
+__host__ __device__ constexpr int plane_dir(int mode, int q)
+{
+    return q < 7 * mode_NE(mode) ? q / mode_NE(mode) : (q - 7 * mode_NE(mode)) / mode_NH(mode);
+}
+__host__ __device__ constexpr int plane_slot(int mode, int q)
+{
+    return q < 7 * mode_NE(mode) ? q % mode_NE(mode)
+                                 : mode_NE(mode) + (q - 7 * mode_NE(mode)) % mode_NH(mode);
+}
+__host__ __device__ constexpr int slot_plane(int mode, int i, int s)
+{
+    return s < mode_NE(mode) ? i * mode_NE(mode) + s
+                             : 7 * mode_NE(mode) + i * mode_NH(mode) + (s - mode_NE(mode));
+}
+__host__ __device__ constexpr int group_first(int nc, int elem_bytes, int s)
+{
+    return nc == 3 ? (s < 2 ? 0 : 2) : (elem_bytes == 4 ? (s & ~1) : (s < 4 ? 0 : 4));
+}
+__host__ __device__ constexpr int group_width(int nc, int elem_bytes, int s)
+{
+    return nc == 3 ? (s < 2 ? 2 : 1) : (elem_bytes == 4 ? 2 : (s < 4 ? 4 : 2));
+}
+// Element index of plane q, cell c (c = z*ny*nxp + y*nxp + x).
+__host__ __device__ inline long long pop_index(int mode, int elem_bytes, long long P, int q, long long c)
+{
+    const int nc = mode_NE(mode) + mode_NH(mode);
+    const int i = plane_dir(mode, q), s = plane_slot(mode, q);
+    const int s0 = group_first(nc, elem_bytes, s), w = group_width(nc, elem_bytes, s);
+    return ((long long)i * nc + s0) * P + (long long)w * c + (s - s0);
+}
+
 // ------------------------------------------------ device helpers shared by
 // the step, adjoint and observable kernels
 // x/3 to within rounding: the constant 1/3 split into a float and a remainder,
@@ -226,12 +274,12 @@ cudaError_t launch_far_field_partial(const FarFieldArgs &a, cudaStream_t s);
 
 cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int nz, int nxp,
                            int *bad_flag, cudaStream_t s);
-cudaError_t launch_pack(int storage, const void *f, long long P, int q, float scale, float *out,
+cudaError_t launch_pack(int mode, int storage, const void *f, long long P, int q, float scale, float *out,
                         int nx, int ny, int nz, int nxp, const IncView &inc, cudaStream_t s);
-cudaError_t launch_unpack(int storage, void *f, long long P, int q, float inv_scale,
+cudaError_t launch_unpack(int mode, int storage, void *f, long long P, int q, float inv_scale,
                           const float *in, int nx, int ny, int nz, int nxp, const IncView &inc,
                           cudaStream_t s);
-cudaError_t launch_add_incident(int storage, void *f, long long P, int Q, float scale,
+cudaError_t launch_add_incident(int mode, int storage, void *f, long long P, int Q, float scale,
                                 int nx, int ny, int nz, int nxp, const IncView &inc, float sign,
                                 cudaStream_t s);
 cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps,

@@ -260,8 +260,9 @@ __device__ __forceinline__ float inc_at(const IncView &v, int q, int x, int y, i
     return v.line[(size_t)q * v.n + s];
 }
 
+// Plane q of the stored populations: element base + w * cell (pop_index).
 template <class S>
-__global__ void pack_kernel(const S *f, int q, float scale, float *out, int nx, int ny,
+__global__ void pack_kernel(const S *f, int w, int q, float scale, float *out, int nx, int ny,
                             long long ncell, int nxp, IncView inc)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
@@ -269,12 +270,12 @@ __global__ void pack_kernel(const S *f, int q, float scale, float *out, int nx, 
         const int x = (int)(i % nx);
         const long long r = i / nx;
         const int y = (int)(r % ny), z = (int)(r / ny);
-        out[i] = ldv<S>(f + r * nxp + x) * scale + inc_at(inc, q, x, y, z);
+        out[i] = ldv<S>(f + w * (r * nxp + x)) * scale + inc_at(inc, q, x, y, z);
     }
 }
 
 template <class S>
-__global__ void unpack_kernel(S *f, int q, float inv_scale, const float *in, int nx, int ny,
+__global__ void unpack_kernel(S *f, int w, int q, float inv_scale, const float *in, int nx, int ny,
                               long long ncell, int nxp, IncView inc)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
@@ -282,14 +283,14 @@ __global__ void unpack_kernel(S *f, int q, float inv_scale, const float *in, int
         const int x = (int)(i % nx);
         const long long r = i / nx;
         const int y = (int)(r % ny), z = (int)(r / ny);
-        stv<S>(f + r * nxp + x, (in[i] - inc_at(inc, q, x, y, z)) * inv_scale);
+        stv<S>(f + w * (r * nxp + x), (in[i] - inc_at(inc, q, x, y, z)) * inv_scale);
     }
 }
 
 // Convert the stored populations of the total-field box between the scattered
 // part and the total (sign = +1: add the incident line, -1: remove it).
 template <class S>
-__global__ void add_incident_kernel(S *f, long long P, int Q, float scale, int nx, int ny,
+__global__ void add_incident_kernel(int mode, S *f, long long P, int Q, float scale, int nx, int ny,
                                     long long ncell, int nxp, IncView inc, float sign)
 {
     const float inv = 1.0f / scale;
@@ -301,7 +302,7 @@ __global__ void add_incident_kernel(S *f, long long P, int Q, float scale, int n
         for (int q = 0; q < Q; ++q) {
             const float add = inc_at(inc, q, x, y, z);
             if (add == 0.f) continue;
-            S *p = f + q * P + r * nxp + x;
+            S *p = f + pop_index(mode, (int)sizeof(S), P, q, r * nxp + x);
             stv<S>(p, (ldv<S>(p) * scale + sign * add) * inv);
         }
     }
@@ -318,7 +319,7 @@ __device__ __forceinline__ void cell_DB(const S *f, float sc, long long P, long 
     B[0] = B[1] = B[2] = 0.f;
 #pragma unroll
     for (int q = 0; q < PL::Q; ++q) {
-        const float v = ldv<S>(f + q * P + c) * sc + inc_at(inc, q, x, y, z);
+        const float v = ldv<S>(f + pop_index(MODE, (int)sizeof(S), P, q, c)) * sc + inc_at(inc, q, x, y, z);
         if (PL::fam(q) == 0) D[PL::comp(q)] += v;
         else B[PL::comp(q)] += v;
     }
@@ -448,49 +449,55 @@ cudaError_t launch_inv_eps(const float *eps, float *inv_eps, int nx, int ny, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(int storage, const void *f, long long P, int q, float scale, float *out,
-                        int nx, int ny, int nz, int nxp, const IncView &inc, cudaStream_t s)
+cudaError_t launch_pack(int mode, int storage, const void *f, long long P, int q, float scale,
+                        float *out, int nx, int ny, int nz, int nxp, const IncView &inc, cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
     const int g = grid_for(n, 256);
+    const int eb = storage == 0 ? 4 : 2;
+    const long long base = pop_index(mode, eb, P, q, 0);
+    const int w = (int)(pop_index(mode, eb, P, q, 1) - base);
     if (storage == 0)
-        pack_kernel<float><<<g, 256, 0, s>>>((const float *)f + q * P, q, scale, out, nx, ny, n, nxp, inc);
+        pack_kernel<float><<<g, 256, 0, s>>>((const float *)f + base, w, q, scale, out, nx, ny, n, nxp, inc);
     else if (storage == 1)
-        pack_kernel<__half><<<g, 256, 0, s>>>((const __half *)f + q * P, q, scale, out, nx, ny, n, nxp, inc);
+        pack_kernel<__half><<<g, 256, 0, s>>>((const __half *)f + base, w, q, scale, out, nx, ny, n, nxp, inc);
     else
-        pack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16 *)f + q * P, q, scale, out, nx,
+        pack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16 *)f + base, w, q, scale, out, nx,
                                                      ny, n, nxp, inc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(int storage, void *f, long long P, int q, float inv_scale,
+cudaError_t launch_unpack(int mode, int storage, void *f, long long P, int q, float inv_scale,
                           const float *in, int nx, int ny, int nz, int nxp, const IncView &inc,
                           cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
     const int g = grid_for(n, 256);
+    const int eb = storage == 0 ? 4 : 2;
+    const long long base = pop_index(mode, eb, P, q, 0);
+    const int w = (int)(pop_index(mode, eb, P, q, 1) - base);
     if (storage == 0)
-        unpack_kernel<float><<<g, 256, 0, s>>>((float *)f + q * P, q, inv_scale, in, nx, ny, n, nxp, inc);
+        unpack_kernel<float><<<g, 256, 0, s>>>((float *)f + base, w, q, inv_scale, in, nx, ny, n, nxp, inc);
     else if (storage == 1)
-        unpack_kernel<__half><<<g, 256, 0, s>>>((__half *)f + q * P, q, inv_scale, in, nx, ny, n, nxp, inc);
+        unpack_kernel<__half><<<g, 256, 0, s>>>((__half *)f + base, w, q, inv_scale, in, nx, ny, n, nxp, inc);
     else
-        unpack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)f + q * P, q, inv_scale, in, nx,
+        unpack_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)f + base, w, q, inv_scale, in, nx,
                                                        ny, n, nxp, inc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_add_incident(int storage, void *f, long long P, int Q, float scale,
+cudaError_t launch_add_incident(int mode, int storage, void *f, long long P, int Q, float scale,
                                 int nx, int ny, int nz, int nxp, const IncView &inc, float sign,
                                 cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
     const int g = grid_for(n, 256);
     if (storage == 0)
-        add_incident_kernel<float><<<g, 256, 0, s>>>((float *)f, P, Q, scale, nx, ny, n, nxp, inc, sign);
+        add_incident_kernel<float><<<g, 256, 0, s>>>(mode, (float *)f, P, Q, scale, nx, ny, n, nxp, inc, sign);
     else if (storage == 1)
-        add_incident_kernel<__half><<<g, 256, 0, s>>>((__half *)f, P, Q, scale, nx, ny, n, nxp, inc, sign);
+        add_incident_kernel<__half><<<g, 256, 0, s>>>(mode, (__half *)f, P, Q, scale, nx, ny, n, nxp, inc, sign);
     else
-        add_incident_kernel<__nv_bfloat16><<<g, 256, 0, s>>>((__nv_bfloat16 *)f, P, Q, scale, nx, ny, n,
+        add_incident_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(mode, (__nv_bfloat16 *)f, P, Q, scale, nx, ny, n,
                                                              nxp, inc, sign);
     return cudaGetLastError();
 }

@@ -39,10 +39,13 @@
 // during step n the lattice reads line(n+1) and the first blocks of the same
 // launch write line(n+2).
 //
-// Memory layout: structure of arrays, one plane per (family, direction,
-// component) of nz*ny*nxp elements, x fastest and padded to a multiple of
-// 32 elements; 4 B of 1/eps_r per cell.  Each population is read once and
-// written once per step: B_cell = 2 Q s + 4 bytes.  The update is a
+// Memory layout: per velocity direction, the direction's populations in
+// groups of 2 (FP32) or 4 and 2 (16-bit, 3D) consecutive values per cell, each
+// group a plane-sized array of nz*ny*nxp cells, x fastest and padded to a
+// multiple of 32 cells (pop_index in lbem_internal.cuh); 4 B of 1/eps_r per
+// cell.  One vector load fetches a group, so a 3D cell takes 21 (FP32) or
+// 14 (16-bit) loads.  Each population is read once and written once per
+// step: B_cell = 2 Q s + 4 bytes.  The update is a
 // memory-bound stencil (~1 flop/byte), so it runs on the CUDA cores; no
 // tensor-core path applies.
 #include <type_traits>
@@ -289,32 +292,132 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
     }
 }
 
-__device__ __forceinline__ void block_row(const StepArgs &a, int b, int &x_block, int &y, int &z)
+// Vector access to one group of a cell's populations (the storage layout is
+// described with pop_index): W = 1, 2 or 4 consecutive slots in one load or
+// store, converted to or from FP32; 16-bit pairs use the paired conversions.
+template <class S> struct Io;
+template <> struct Io<float> {
+    static __device__ __forceinline__ void ld1(const void *p, int k, float &a)
+    {
+        a = __ldg(static_cast<const float *>(p) + k);
+    }
+    static __device__ __forceinline__ void ld2(const void *p, int k, float &a, float &b)
+    {
+        const float2 v = __ldg(static_cast<const float2 *>(p) + k);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st1(void *p, int k, float a) { static_cast<float *>(p)[k] = a; }
+    static __device__ __forceinline__ void st2(void *p, int k, float a, float b)
+    {
+        static_cast<float2 *>(p)[k] = make_float2(a, b);
+    }
+};
+template <class H, class H2> struct Io16 {
+    static __device__ __forceinline__ float2 unpack(unsigned u)
+    {
+        H2 h;
+        memcpy(&h, &u, 4);
+        if constexpr (std::is_same<H, __half>::value) return __half22float2(h);
+        else return __bfloat1622float2(h);
+    }
+    static __device__ __forceinline__ unsigned pack(float a, float b)
+    {
+        H2 h;
+        if constexpr (std::is_same<H, __half>::value) h = __floats2half2_rn(a, b);
+        else h = __floats2bfloat162_rn(a, b);
+        unsigned u;
+        memcpy(&u, &h, 4);
+        return u;
+    }
+    static __device__ __forceinline__ void ld1(const void *p, int k, float &a)
+    {
+        const H v = __ldg(static_cast<const H *>(p) + k);
+        if constexpr (std::is_same<H, __half>::value) a = __half2float(v);
+        else a = __bfloat162float(v);
+    }
+    static __device__ __forceinline__ void ld2(const void *p, int k, float &a, float &b)
+    {
+        const float2 v = unpack(__ldg(static_cast<const unsigned *>(p) + k));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void ld4(const void *p, int k, float &a, float &b, float &c, float &d)
+    {
+        const uint2 u = __ldg(static_cast<const uint2 *>(p) + k);
+        const float2 v0 = unpack(u.x), v1 = unpack(u.y);
+        a = v0.x;
+        b = v0.y;
+        c = v1.x;
+        d = v1.y;
+    }
+    static __device__ __forceinline__ void st1(void *p, int k, float a)
+    {
+        if constexpr (std::is_same<H, __half>::value) static_cast<H *>(p)[k] = __float2half_rn(a);
+        else static_cast<H *>(p)[k] = __float2bfloat16_rn(a);
+    }
+    static __device__ __forceinline__ void st2(void *p, int k, float a, float b)
+    {
+        static_cast<unsigned *>(p)[k] = pack(a, b);
+    }
+    static __device__ __forceinline__ void st4(void *p, int k, float a, float b, float c, float d)
+    {
+        static_cast<uint2 *>(p)[k] = make_uint2(pack(a, b), pack(c, d));
+    }
+};
+template <> struct Io<__half> : Io16<__half, __half2> {};
+template <> struct Io<__nv_bfloat16> : Io16<__nv_bfloat16, __nv_bfloat162> {};
+
+// All populations of one cell: direction i's groups read at cell index src[i]
+// (load) or written at c (store); f is indexed by population plane.
+template <int MODE, class S>
+__device__ __forceinline__ void load_cell(const StepArgs &a, const int src[7], float *f)
 {
-    x_block = b % a.nblk_x;
-    const int row = b / a.nblk_x;
-    y = row % a.ny;
-    z = row / a.ny;
+    constexpr int NC = Planes<MODE>::NC;
+#define SQ(s) f[slot_plane(MODE, i, s)]
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const void *const *b = a.fin_q + i * NC;
+        if constexpr (NC == 3) {
+            Io<S>::ld2(b[0], src[i], SQ(0), SQ(1));
+            Io<S>::ld1(b[2], src[i], SQ(2));
+        } else if constexpr (sizeof(S) == 4) {
+            Io<S>::ld2(b[0], src[i], SQ(0), SQ(1));
+            Io<S>::ld2(b[2], src[i], SQ(2), SQ(3));
+            Io<S>::ld2(b[4], src[i], SQ(4), SQ(5));
+        } else {
+            Io<S>::ld4(b[0], src[i], SQ(0), SQ(1), SQ(2), SQ(3));
+            Io<S>::ld2(b[4], src[i], SQ(4), SQ(5));
+        }
+    }
 }
 
-template <class S> __device__ __forceinline__ float load_pop(const S *p);
-template <> __device__ __forceinline__ float load_pop<float>(const float *p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_pop<__half>(const __half *p) { return __half2float(__ldg(p)); }
-template <> __device__ __forceinline__ float load_pop<__nv_bfloat16>(const __nv_bfloat16 *p) {
-    return __bfloat162float(__ldg(p));
-}
-template <class S> __device__ __forceinline__ void store_pop(S *p, float v);
-template <> __device__ __forceinline__ void store_pop<float>(float *p, float v) { *p = v; }
-template <> __device__ __forceinline__ void store_pop<__half>(__half *p, float v) { *p = __float2half_rn(v); }
-template <> __device__ __forceinline__ void store_pop<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
-    *p = __float2bfloat16_rn(v);
+template <int MODE, class S>
+__device__ __forceinline__ void store_cell(const StepArgs &a, int c, const float *f)
+{
+    constexpr int NC = Planes<MODE>::NC;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        void *const *b = a.fout_q + i * NC;
+        if constexpr (NC == 3) {
+            Io<S>::st2(b[0], c, SQ(0), SQ(1));
+            Io<S>::st1(b[2], c, SQ(2));
+        } else if constexpr (sizeof(S) == 4) {
+            Io<S>::st2(b[0], c, SQ(0), SQ(1));
+            Io<S>::st2(b[2], c, SQ(2), SQ(3));
+            Io<S>::st2(b[4], c, SQ(4), SQ(5));
+        } else {
+            Io<S>::st4(b[0], c, SQ(0), SQ(1), SQ(2), SQ(3));
+            Io<S>::st2(b[4], c, SQ(4), SQ(5));
+        }
+    }
+#undef SQ
 }
 
-// One thread per cell of a row.  Plane q of the input/output buffers starts
-// at a.fin_q[q] / a.fout_q[q] (kernel parameters), so every access is a
-// 32-bit in-plane offset from a constant-bank base; the +-x pulls are plain
-// loads shifted by one element (coalesced; the extra sector per warp hits in
-// L1/L2).
+// One thread per cell.  The input group of direction i starts at
+// a.fin_q[i * NC + s0] (kernel parameters), so every access is a 32-bit
+// in-group offset from a constant-bank base; the +-x pulls are plain loads
+// shifted by one element (coalesced; the extra sector per warp hits in L1/L2).
 // The cells x = bx * BX + threadIdx.x of row (y, z) for one step.
 template <int MODE, class S, int BX, bool REC = false>
 __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int z)
@@ -336,25 +439,32 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
     src[6] = c + (z < a.nz - 1 ? pz : 0);
 
     float f[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) f[q] = load_pop<S>(static_cast<const S *>(a.fin_q[q]) + src[PL::dir(q)]);
+    load_cell<MODE, S>(a, src, f);
     FloatCell cell{f};
     update_cell<MODE, REC>(cell, x, y, z, __ldg(a.inv_eps + c), a);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) store_pop<S>(static_cast<S *>(a.fout_q[q]) + c, f[q]);
+    store_cell<MODE, S>(a, c, f);
 }
 
+// One block per tile of BX cells x rows_of<S> consecutive rows (y fastest,
+// then z); the first blocks also update the incident line.  Blocks of several
+// rows cut the per-block start-up cost of short 128-cell rows; 72 registers
+// (7 blocks of 128 threads per SM) hold a cell without spilling.  Both were
+// chosen by timing the 384^3 sphere on GB300.
+template <class S> __host__ __device__ constexpr int rows_of() { return sizeof(S) == 4 ? 2 : 4; }
+
 template <int MODE, class S, int BX, bool REC = false>
-__global__ void __launch_bounds__(BX, sizeof(S) == 4 ? 6 : 7) step_kernel_cell(const StepArgs a)
+__global__ void __launch_bounds__(BX, 7) step_kernel_cell(const StepArgs a)
 {
+    constexpr int R = rows_of<S>();
     const int b = blockIdx.x;
     if (a.line_on) {
         const int s = b * BX + threadIdx.x;
         if (s < a.n_line) line_work<MODE>(a, s);
     }
-    int bx, y, z;
-    block_row(a, b, bx, y, z);
-    row_cells<MODE, S, BX, REC>(a, bx, y, z);
+    const int bx = b % a.nblk_x;
+    const int r0 = (b / a.nblk_x) * R;
+    const int r1 = min(r0 + R, a.ny * a.nz);
+    for (int r = r0; r < r1; ++r) row_cells<MODE, S, BX, REC>(a, bx, r % a.ny, r / a.ny);
 }
 
 constexpr int kBX = 128;  // threads per block = cells per row tile
@@ -506,7 +616,8 @@ template <int MODE, class S, bool REC = false>
 cudaError_t launch_cell(StepArgs a, cudaStream_t s)
 {
     a.nblk_x = (a.nx + kBX - 1) / kBX;
-    a.nblk_main = a.nblk_x * a.ny * a.nz;
+    a.rows_per_block = rows_of<S>();
+    a.nblk_main = a.nblk_x * ((a.ny * a.nz + a.rows_per_block - 1) / a.rows_per_block);
     if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
     if (REC && a.rec == nullptr) return cudaErrorInvalidValue;
     step_kernel_cell<MODE, S, kBX, REC><<<a.nblk_main, kBX, 0, s>>>(a);
