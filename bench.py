@@ -157,6 +157,24 @@ def angles():
 
 
 # ------------------------------------------------------------------ GPU arm
+def max_over_ranks(t_ms: float, world: int, device=None) -> float:
+    """The job's time: the slowest rank's timed region (all-reduce MAX over the
+    default process group; NCCL on GPUs, any backend works)."""
+    if world == 1:
+        return t_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells: int, updates_per_step: int, steps: int, world: int, t_ms: float) -> float:
+    """Whole-job throughput: every rank advances its own replica of the
+    workload, so the job updates cells x updates x steps x world sites."""
+    return cells * updates_per_step * steps * world / (t_ms / 1e3) / 1e6
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2510_11042_gb300 import build as lib_build
@@ -261,17 +279,11 @@ def run_gpu(args, rank, world, local_rank):
             secondary[st] = one_storage(st, K, Wm, False)
 
     # max over ranks of the timed region
-    t_main = main["total_ms"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_main], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_main = float(t.item())
+    t_main = max_over_ranks(main["total_ms"], world, dev)
     if rank != 0:
         return
     hbm, peak_kind = peaks()
-    ups = cells * T * K * world
-    value = ups / (t_main / 1e3) / 1e6
+    value = job_mlups(cells, T, K, world, t_main)
     bc = b_cell("3d", "f32")
     achieved = bc * cells / (main["kernel_ms"] / 1e3) / 1e9
     traffic = traffic_from_profile(f"sphere_{args.size}", "f32")
