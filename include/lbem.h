@@ -157,6 +157,16 @@ int32_t lbem_step(lbem_handle h, int64_t n);
 /* Number of steps taken since creation (the time of the stored state). */
 int32_t lbem_get_time(lbem_handle h, int64_t *t_out);
 
+/* Magnetic media: a per-cell relative permeability map (nx*ny*nz floats, x
+ * fastest; host or device), validated like eps_r (finite, >= 1, else
+ * LBEM_ERR_ARG with the handle unchanged).  Eq. 2's rest population becomes
+ * h_0^eq = (mu_r - 1) H with H = B / mu_r, and the TF/SF source of magnetic
+ * cells carries the field H_inc (1/mu_r - 1).  Every step then reads 4 more
+ * bytes per cell.  mu_r == NULL returns to mu_r = 1 everywhere.  The paper
+ * uses mu_r != 1 only in its 1D interface tests (Sec. 3.1, Eq. 11).  Batched
+ * runs and the adjoint support mu_r = 1 only. */
+int32_t lbem_set_permeability(lbem_handle h, const float *mu_r, int32_t mu_on_device);
+
 /* Angular scattering intensity |S|^2 (Eqs. 5, 6) by the near-to-far-field
  * projection of Eqs. 7-10 in the far-field limit, from the DFT accumulators:
  * J = n x H, M = -n x E on the NTFF box faces (trapezoidal rule per face),

@@ -288,8 +288,8 @@ class Run:
         self.t = 0  # steps done; state holds f*(t)
         w = problem.wave
         nx, ny, nz = problem.shape
-        self.main = Lattice(problem.shape, problem.eps, sponge_w=problem.absorber_width,
-                            sigma_max=problem.sigma_max)
+        self.main = Lattice(problem.shape, problem.eps, mu=getattr(problem, "mu", None),
+                            sponge_w=problem.absorber_width, sigma_max=problem.sigma_max)
         self.T = int(round(3 * w.wavelength))
         if abs(3 * w.wavelength - self.T) > 1e-9:
             raise ValueError("3*wavelength must be an integer (the period in steps)")

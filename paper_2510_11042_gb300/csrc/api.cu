@@ -29,6 +29,8 @@ struct lbem_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     float *inv_eps = nullptr;
+    float *inv_mu = nullptr;    // 1/mu_r plane; used only when mu_on
+    bool mu_on = false;
     float *line[3] = {nullptr, nullptr, nullptr};  // incident line at t, t+1, t+2 (mod 3)
     int n_line_max = 0;
     double *dft = nullptr;
@@ -103,7 +105,7 @@ static int check_status(lbem_ctx *h)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t f0, f1, inv_eps, line0, line1, line2, dft, line_dft, scratch, stage, flag, total;
+    size_t f0, f1, inv_eps, inv_mu, line0, line1, line2, dft, line_dft, scratch, stage, flag, total;
     int Q, nxp, n_line_max;
     long long P, ncell;
     size_t elem, dft_doubles_max, scratch_doubles;
@@ -151,6 +153,7 @@ static Layout make_layout(const lbem_grid_desc *g)
     L.f0 = take((size_t)L.Q * L.P * L.elem);
     L.f1 = take((size_t)L.Q * L.P * L.elem);
     L.inv_eps = take((size_t)L.P * 4);
+    L.inv_mu = take((size_t)L.P * 4);
     L.line0 = take((size_t)L.Q * L.n_line_max * 4);
     L.line1 = take((size_t)L.Q * L.n_line_max * 4);
     L.line2 = take((size_t)L.Q * L.n_line_max * 4);
@@ -216,6 +219,7 @@ static void fill_common_args(lbem_ctx *h, StepArgs &a)
 {
     std::memset(&a, 0, sizeof a);
     a.inv_eps = h->inv_eps;
+    a.inv_mu = h->mu_on ? h->inv_mu : nullptr;
     a.nx = h->g.nx; a.ny = h->g.ny; a.nz = h->g.nz; a.nxp = h->nxp;
     a.P = h->P;
     a.w = h->g.absorber_width;
@@ -256,7 +260,15 @@ int32_t lbem_workspace_bytes(const lbem_grid_desc *grid, size_t *bytes_out)
     return LBEM_OK;
 }
 
+static int upload_inverse(lbem_ctx *h, const float *v, int on_device, float *target, const char *name);
+
 static int upload_eps(lbem_ctx *h, const float *eps, int on_device)
+{
+    return upload_inverse(h, eps, on_device, h->inv_eps, "eps_r");
+}
+
+// Validate a per-cell map (finite, >= 1) and store its reciprocal in target.
+static int upload_inverse(lbem_ctx *h, const float *eps, int on_device, float *target, const char *name)
 {
     const float *src = eps;
     if (!on_device) {
@@ -270,8 +282,8 @@ static int upload_eps(lbem_ctx *h, const float *eps, int on_device)
     int bad = 0;
     CK(h, cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (bad) return fail(h, LBEM_ERR_ARG, "eps_r must be finite and >= 1 in every cell");
-    CK(h, launch_inv_eps(src, h->inv_eps, h->g.nx, h->g.ny, h->g.nz, h->nxp, h->flag, h->stream));
+    if (bad) return fail(h, LBEM_ERR_ARG, "%s must be finite and >= 1 in every cell", name);
+    CK(h, launch_inv_eps(src, target, h->g.nx, h->g.ny, h->g.nz, h->nxp, h->flag, h->stream));
     h->launches += 1;
     return LBEM_OK;
 }
@@ -322,6 +334,7 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->f[0] = h->ws + L.f0;
     h->f[1] = h->ws + L.f1;
     h->inv_eps = (float *)(h->ws + L.inv_eps);
+    h->inv_mu = (float *)(h->ws + L.inv_mu);
     h->line[0] = (float *)(h->ws + L.line0);
     h->line[1] = (float *)(h->ws + L.line1);
     h->line[2] = (float *)(h->ws + L.line2);
@@ -356,6 +369,19 @@ int32_t lbem_set_permittivity(lbem_handle h, const float *eps_r, int32_t eps_on_
     if (!eps_r) return fail(h, LBEM_ERR_ARG, "eps_r is NULL");
     h->adj_valid = false;
     return upload_eps(h, eps_r, eps_on_device);
+}
+
+int32_t lbem_set_permeability(lbem_handle h, const float *mu_r, int32_t mu_on_device)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    h->adj_valid = false;
+    if (!mu_r) {
+        h->mu_on = false;
+        return LBEM_OK;
+    }
+    const int rc = upload_inverse(h, mu_r, mu_on_device, h->inv_mu, "mu_r");
+    if (rc == LBEM_OK) h->mu_on = true;
+    return rc;
 }
 
 static int axis_of(const double d[3])
@@ -515,7 +541,8 @@ int32_t lbem_step(lbem_handle h, int64_t n)
                 a.dft_scale_cells = a.dft_scale * h->scale;            // lattice (storage units)
             }
         }
-        cudaError_t e = launch_step(h->g.mode, h->g.storage, a, h->stream);
+        cudaError_t e = h->mu_on ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
+                                 : launch_step(h->g.mode, h->g.storage, a, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
         h->launches += 1;
         h->cur ^= 1;
@@ -581,6 +608,8 @@ extern "C" int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, 
         if (!handles[i]) return bfail(nullptr, LBEM_ERR_ARG, "handle %d is NULL", i);
         if (handles[i]->g.mode != handles[0]->g.mode || handles[i]->g.storage != handles[0]->g.storage)
             return bfail(nullptr, LBEM_ERR_ARG, "all handles of a batch need the same mode and storage");
+        if (handles[i]->mu_on)
+            return bfail(nullptr, LBEM_ERR_ARG, "batched runs support mu_r = 1 only");
         if (handles[i]->device != dev) return bfail(nullptr, LBEM_ERR_ARG, "handle %d is on another device", i);
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return bfail(nullptr, LBEM_ERR_ARG, "handle %d repeated", i);
@@ -905,7 +934,7 @@ int32_t lbem_fields(lbem_handle h, float *E, float *H, int32_t on_device)
     for (int comp = 0; comp < 6; ++comp) {
         float *dst = (comp < 3 ? E : H) + (size_t)(comp % 3) * h->ncell;
         float *out = on_device ? dst : h->stage;
-        CK(h, launch_fields(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->scale, h->P,
+        CK(h, launch_fields(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->mu_on ? h->inv_mu : nullptr, h->scale, h->P,
                             h->g.nx, h->g.ny, h->g.nz, h->nxp, inc_view(h), comp, out, h->stream));
         h->launches += 1;
         if (!on_device) {
@@ -940,7 +969,7 @@ int32_t lbem_energy(lbem_handle h, double *out)
     double *d_out = h->scratch;
     double *part = h->scratch + 8;
     int l = 0;
-    CK(h, launch_energy(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->scale, h->P, h->g.nx,
+    CK(h, launch_energy(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->mu_on ? h->inv_mu : nullptr, h->scale, h->P, h->g.nx,
                         h->g.ny, h->g.nz, h->nxp, inc_view(h), part, (int)(h->scratch_doubles - 8),
                         d_out, h->stream, &l));
     h->launches += l;
@@ -1127,6 +1156,7 @@ int32_t lbem_forward_checkpointed(lbem_handle h, int64_t n_steps, int32_t K, voi
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
     if (n_steps < 1 || K < 1) return fail(h, LBEM_ERR_ARG, "need n_steps >= 1 and K >= 1");
     if (h->g.storage != LBEM_F32) return fail(h, LBEM_ERR_ARG, "the adjoint needs FP32 storage");
+    if (h->mu_on) return fail(h, LBEM_ERR_ARG, "the adjoint supports mu_r = 1 only");
     if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
     if (h->t != 0) return fail(h, LBEM_ERR_STATE, "the checkpointed run must start at t = 0 (got t = %lld)",
                                (long long)h->t);

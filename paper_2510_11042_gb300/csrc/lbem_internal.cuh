@@ -155,6 +155,7 @@ struct StepArgs {
     const void *fin_q[kMaxQ];  // start of each input population plane
     void *fout_q[kMaxQ];       // start of each output population plane
     const float *inv_eps;
+    const float *inv_mu;       // 1/mu_r per cell (the magnetic-media kernel only)
     int nx, ny, nz, nxp;       // extent and padded row pitch (elements)
     long long P;               // plane stride in elements = nz*ny*nxp
     int nblk_x;                // blocks per row (set by the launcher)
@@ -229,6 +230,8 @@ struct BatchArgs {
 cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cudaStream_t s);
 int batch_max_blocks_per_sm(int mode, int storage);
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
+// The step kernel with a per-cell mu_r (a.inv_mu), Eq. 2's h_0 = (mu_r - 1) H
+cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_line_init(int mode, const StepArgs &a, cudaStream_t s);
 // The step kernel with a.rec written (FP32 storage; forward replay of the adjoint)
 cudaError_t launch_step_record(int mode, const StepArgs &a, cudaStream_t s);
@@ -282,10 +285,10 @@ cudaError_t launch_unpack(int mode, int storage, void *f, long long P, int q, fl
 cudaError_t launch_add_incident(int mode, int storage, void *f, long long P, int Q, float scale,
                                 int nx, int ny, int nz, int nxp, const IncView &inc, float sign,
                                 cudaStream_t s);
-cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps,
+cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps, const float *inv_mu,
                           float scale, long long P, int nx, int ny, int nz, int nxp,
                           const IncView &inc, int comp, float *out, cudaStream_t s);
-cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps,
+cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps, const float *inv_mu,
                           float scale, long long P, int nx, int ny, int nz, int nxp,
                           const IncView &inc, double *partial, int max_partial, double *out,
                           cudaStream_t s, int *launches);

@@ -327,8 +327,9 @@ __device__ __forceinline__ void cell_DB(const S *f, float sc, long long P, long 
 
 // One field component per launch: comp 0..2 -> E_x..E_z, 3..5 -> H_x..H_z.
 template <int MODE, class S>
-__global__ void fields_kernel(const S *f, const float *inv_eps, float sc, long long P, int nx,
-                              int ny, long long ncell, int nxp, IncView inc, int comp, float *out)
+__global__ void fields_kernel(const S *f, const float *inv_eps, const float *inv_mu, float sc,
+                              long long P, int nx, int ny, long long ncell, int nxp, IncView inc,
+                              int comp, float *out)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
          i += (long long)gridDim.x * blockDim.x) {
@@ -337,7 +338,7 @@ __global__ void fields_kernel(const S *f, const float *inv_eps, float sc, long l
         const long long c = r * nxp + x;
         float D[3], B[3];
         cell_DB<MODE, S>(f, sc, P, c, inc, x, (int)(r % ny), (int)(r / ny), D, B);
-        out[i] = comp < 3 ? D[comp] * inv_eps[c] : B[comp - 3];
+        out[i] = comp < 3 ? D[comp] * inv_eps[c] : B[comp - 3] * (inv_mu ? inv_mu[c] : 1.0f);
     }
 }
 
@@ -345,6 +346,7 @@ constexpr int kEThreads = 256;
 
 template <int MODE, class S>
 __global__ void __launch_bounds__(kEThreads) energy_partial(const S *f, const float *inv_eps,
+                                                            const float *inv_mu,
                                                             float sc, long long P, int nx, int ny,
                                                             long long ncell, int nxp, IncView inc,
                                                             double *partial)
@@ -357,10 +359,10 @@ __global__ void __launch_bounds__(kEThreads) energy_partial(const S *f, const fl
         const long long c = r * nxp + x;
         float D[3], B[3];
         cell_DB<MODE, S>(f, sc, P, c, inc, x, (int)(r % ny), (int)(r / ny), D, B);
-        const double ie = inv_eps[c];
-        // 1/2 (eps |E|^2 + |H|^2) = 1/2 (|D|^2 / eps + |B|^2)
+        const double ie = inv_eps[c], im = inv_mu ? (double)inv_mu[c] : 1.0;
+        // 1/2 (eps |E|^2 + mu |H|^2) = 1/2 (|D|^2 / eps + |B|^2 / mu)
         acc += 0.5 * (((double)D[0] * D[0] + (double)D[1] * D[1] + (double)D[2] * D[2]) * ie +
-                      (double)B[0] * B[0] + (double)B[1] * B[1] + (double)B[2] * B[2]);
+                      ((double)B[0] * B[0] + (double)B[1] * B[1] + (double)B[2] * B[2]) * im);
     }
     __shared__ double red[kEThreads / 32];
     const double v = warp_sum(acc);
@@ -503,26 +505,26 @@ cudaError_t launch_add_incident(int mode, int storage, void *f, long long P, int
 }
 
 template <int MODE, class S>
-static cudaError_t fields_t(const void *f, const float *inv_eps, float sc, long long P,
-                            int nx, int ny, int nz, int nxp, const IncView &inc, int comp,
-                            float *out, cudaStream_t s)
+static cudaError_t fields_t(const void *f, const float *inv_eps, const float *inv_mu, float sc,
+                            long long P, int nx, int ny, int nz, int nxp, const IncView &inc,
+                            int comp, float *out, cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
-    fields_kernel<MODE, S><<<grid_for(n, 256), 256, 0, s>>>((const S *)f, inv_eps, sc, P, nx, ny, n,
-                                                             nxp, inc, comp, out);
+    fields_kernel<MODE, S><<<grid_for(n, 256), 256, 0, s>>>((const S *)f, inv_eps, inv_mu, sc, P, nx,
+                                                             ny, n, nxp, inc, comp, out);
     return cudaGetLastError();
 }
 
 template <int MODE, class S>
-static cudaError_t energy_t(const void *f, const float *inv_eps, float sc, long long P,
+static cudaError_t energy_t(const void *f, const float *inv_eps, const float *inv_mu, float sc, long long P,
                             int nx, int ny, int nz, int nxp, const IncView &inc, double *partial,
                             int max_partial, double *out, cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
     int g = grid_for(n, kEThreads);
     if (g > max_partial) g = max_partial;
-    energy_partial<MODE, S><<<g, kEThreads, 0, s>>>((const S *)f, inv_eps, sc, P, nx, ny, n, nxp, inc,
-                                                     partial);
+    energy_partial<MODE, S><<<g, kEThreads, 0, s>>>((const S *)f, inv_eps, inv_mu, sc, P, nx, ny, n, nxp,
+                                                     inc, partial);
     sum_partials<<<1, 32, 0, s>>>(partial, g, out);
     return cudaGetLastError();
 }
@@ -541,20 +543,20 @@ static cudaError_t energy_t(const void *f, const float *inv_eps, float sc, long 
     default: return cudaErrorInvalidValue;                                       \
     }
 
-cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps,
+cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps, const float *inv_mu,
                           float scale, long long P, int nx, int ny, int nz, int nxp,
                           const IncView &inc, int comp, float *out, cudaStream_t s)
 {
-    LBEM_DISPATCH(fields_t, f, inv_eps, scale, P, nx, ny, nz, nxp, inc, comp, out, s)
+    LBEM_DISPATCH(fields_t, f, inv_eps, inv_mu, scale, P, nx, ny, nz, nxp, inc, comp, out, s)
 }
 
-cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps,
+cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps, const float *inv_mu,
                           float scale, long long P, int nx, int ny, int nz, int nxp,
                           const IncView &inc, double *partial, int max_partial, double *out,
                           cudaStream_t s, int *launches)
 {
     if (launches) *launches += 2;
-    LBEM_DISPATCH(energy_t, f, inv_eps, scale, P, nx, ny, nz, nxp, inc, partial, max_partial, out, s)
+    LBEM_DISPATCH(energy_t, f, inv_eps, inv_mu, scale, P, nx, ny, nz, nxp, inc, partial, max_partial, out, s)
 }
 
 }  // namespace lbem

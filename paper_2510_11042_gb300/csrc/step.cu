@@ -5,11 +5,12 @@
 //   pull    f_i(r) = f*_i(clamp(r - c_i))           (Eq. 1 streaming + Eq. 4)
 //   TF/SF   incident population of the link's source cell added on links that
 //           enter the total-field box, removed on links that leave it
-//   moments D = sum_i e_i, B = sum_i h_i, E = D / eps_r, H = B  (mu_r = 1)
+//   moments D = sum_i e_i, B = sum_i h_i, E = D / eps_r, H = B / mu_r
+//           (mu_r = 1 unless a permeability map is set)
 //   DFT     X += x(t) exp(-j w t) on the NTFF box surface (FP64 accumulators)
 //   collide f* = 2 f_eq - f (tau = 1/2, equilibria of Eq. 2):
 //             e_0* = 2 (eps_r - 1) E - e_0 = 2 (D - E) - e_0
-//             e_i* = (E - c_i x H) / 3 - e_i,    h_0* = -h_0,
+//             e_i* = (E - c_i x H) / 3 - e_i,    h_0* = 2 (B - H) - h_0,
 //             h_i* = (H + c_i x E) / 3 - h_i
 //           with E/3 and H/3 free of rounding bias, so that the sum of the moving
 //           equilibria, 6 (E/3), carries no systematic rounding bias and D, B
@@ -178,9 +179,9 @@ struct FloatCell {
 // Values are in storage units (population / scale); fields go to the DFT
 // multiplied back by the scale (dft_scale_cells), the incident source is
 // divided by it.
-template <int MODE, bool REC = false, class Cell>
+template <int MODE, bool REC = false, bool MU = false, class Cell>
 __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float inv_eps,
-                                            const StepArgs &a)
+                                            const StepArgs &a, float inv_mu = 1.0f)
 {
     using PL = Planes<MODE>;
     using M = Mode<MODE>;
@@ -206,9 +207,12 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
         for (int k = 0; k < PL::NE; ++k)
             a.rec[(long long)k * a.P + c] = D[M::ec(k)] * a.scale + Dinc[M::ec(k)];
     }
-    float E[3], E3[3] = {0.f, 0.f, 0.f}, H3[3] = {0.f, 0.f, 0.f};
+    float E[3], H[3], E3[3] = {0.f, 0.f, 0.f}, H3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int c3 = 0; c3 < 3; ++c3) E[c3] = D[c3] * inv_eps;
+    for (int c3 = 0; c3 < 3; ++c3) {
+        E[c3] = D[c3] * inv_eps;
+        H[c3] = MU ? B[c3] * inv_mu : B[c3];
+    }
 
     if (a.dft_on && in_box(x, y, z, a.nt_lo, a.nt_hi)) {
         const int g[3] = {x, y, z};
@@ -217,7 +221,7 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
 #pragma unroll
         for (int k = 0; k < PL::NE; ++k) vals[k] = E[M::ec(k)];
 #pragma unroll
-        for (int k = 0; k < PL::NH; ++k) vals[PL::NE + k] = B[M::hc(k)];
+        for (int k = 0; k < PL::NH; ++k) vals[PL::NE + k] = H[M::hc(k)];
         int face = 0;
         for (int ax = 0; ax < 3; ++ax) {
             if (n3[ax] <= 1) continue;
@@ -241,7 +245,7 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
 #pragma unroll
     for (int k = 0; k < PL::NE; ++k) E3[M::ec(k)] = third(E[M::ec(k)]);
 #pragma unroll
-    for (int k = 0; k < PL::NH; ++k) H3[M::hc(k)] = third(B[M::hc(k)]);
+    for (int k = 0; k < PL::NH; ++k) H3[M::hc(k)] = third(H[M::hc(k)]);
 
     int d = min(x, a.nx - 1 - x);
     d = min(d, min(y, a.ny - 1 - y));
@@ -250,7 +254,9 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
 
     // incident-field source of dielectric cells inside the total-field box
     // (the box lies outside the absorbing layer, so keep == 1 there)
-    const bool source = a.tfsf && inv_eps != 1.0f && in_box(x, y, z, a.tf_lo, a.tf_hi);
+    // (with magnetic media also the field dH = H_inc (1/mu_r - 1))
+    const bool source = a.tfsf && (inv_eps != 1.0f || (MU && inv_mu != 1.0f)) &&
+                        in_box(x, y, z, a.tf_lo, a.tf_hi);
     if (!source && keep == 1.0f) {
         // most cells: plain collision, f* = 2 f_eq - f
 #pragma unroll
@@ -258,12 +264,13 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
             const int i = PL::dir(q), ac = PL::comp(q);
             float eq2;
             if (PL::fam(q) == 0) eq2 = (i == 0) ? 2.f * (D[ac] - E[ac]) : E3[ac] - cross_c(i, H3, ac);
-            else eq2 = (i == 0) ? 0.f : H3[ac] + cross_c(i, E3, ac);
+            else eq2 = (i == 0) ? (MU ? 2.f * (B[ac] - H[ac]) : 0.f) : H3[ac] + cross_c(i, E3, ac);
             f.set(q, eq2 - f.get(q));
         }
         return;
     }
     float dE[3] = {0.f, 0.f, 0.f}, dE3[3] = {0.f, 0.f, 0.f};
+    float dH[3] = {0.f, 0.f, 0.f}, dH3[3] = {0.f, 0.f, 0.f};
     if (source) {
         const int sl = a.inc_axis == 0 ? x : (a.inc_axis == 1 ? y : z);
 #pragma unroll
@@ -275,6 +282,17 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
             dE[c3] *= g;
             dE3[c3] = third(dE[c3]);
         }
+        if (MU) {
+#pragma unroll
+            for (int q = 7 * PL::NE; q < Q; ++q)
+                dH[PL::comp(q)] += __ldg(a.line_n1 + (size_t)q * a.n_line + sl);
+            const float gh = (inv_mu - 1.0f) * a.inv_scale;
+#pragma unroll
+            for (int c3 = 0; c3 < 3; ++c3) {
+                dH[c3] *= gh;
+                dH3[c3] = third(dH[c3]);
+            }
+        }
     }
 
 #pragma unroll
@@ -283,10 +301,11 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
         float eq2, src;  // 2 f_eq and the incident source
         if (PL::fam(q) == 0) {
             eq2 = (i == 0) ? 2.f * (D[ac] - E[ac]) : E3[ac] - cross_c(i, H3, ac);
-            src = (i == 0) ? -2.f * dE[ac] : dE3[ac];
+            src = (i == 0) ? -2.f * dE[ac] : (MU ? dE3[ac] - cross_c(i, dH3, ac) : dE3[ac]);
         } else {
-            eq2 = (i == 0) ? 0.f : H3[ac] + cross_c(i, E3, ac);
-            src = (i == 0) ? 0.f : cross_c(i, dE3, ac);
+            eq2 = (i == 0) ? (MU ? 2.f * (B[ac] - H[ac]) : 0.f) : H3[ac] + cross_c(i, E3, ac);
+            src = (i == 0) ? (MU ? -2.f * dH[ac] : 0.f)
+                           : (MU ? dH3[ac] + cross_c(i, dE3, ac) : cross_c(i, dE3, ac));
         }
         f.set(q, (eq2 - f.get(q) + src) * keep);
     }
@@ -419,7 +438,7 @@ __device__ __forceinline__ void store_cell(const StepArgs &a, int c, const float
 // in-group offset from a constant-bank base; the +-x pulls are plain loads
 // shifted by one element (coalesced; the extra sector per warp hits in L1/L2).
 // The cells x = bx * BX + threadIdx.x of row (y, z) for one step.
-template <int MODE, class S, int BX, bool REC = false>
+template <int MODE, class S, int BX, bool REC = false, bool MU = false>
 __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int z)
 {
     using PL = Planes<MODE>;
@@ -441,7 +460,8 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
     float f[Q];
     load_cell<MODE, S>(a, src, f);
     FloatCell cell{f};
-    update_cell<MODE, REC>(cell, x, y, z, __ldg(a.inv_eps + c), a);
+    update_cell<MODE, REC, MU>(cell, x, y, z, __ldg(a.inv_eps + c), a,
+                               MU ? __ldg(a.inv_mu + c) : 1.0f);
     store_cell<MODE, S>(a, c, f);
 }
 
@@ -452,7 +472,7 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
 // chosen by timing the 384^3 sphere on GB300.
 template <class S> __host__ __device__ constexpr int rows_of() { return sizeof(S) == 4 ? 2 : 4; }
 
-template <int MODE, class S, int BX, bool REC = false>
+template <int MODE, class S, int BX, bool REC = false, bool MU = false>
 __global__ void __launch_bounds__(BX, 7) step_kernel_cell(const StepArgs a)
 {
     constexpr int R = rows_of<S>();
@@ -464,7 +484,7 @@ __global__ void __launch_bounds__(BX, 7) step_kernel_cell(const StepArgs a)
     const int bx = b % a.nblk_x;
     const int r0 = (b / a.nblk_x) * R;
     const int r1 = min(r0 + R, a.ny * a.nz);
-    for (int r = r0; r < r1; ++r) row_cells<MODE, S, BX, REC>(a, bx, r % a.ny, r / a.ny);
+    for (int r = r0; r < r1; ++r) row_cells<MODE, S, BX, REC, MU>(a, bx, r % a.ny, r / a.ny);
 }
 
 constexpr int kBX = 128;  // threads per block = cells per row tile
@@ -612,7 +632,7 @@ __global__ void line_init_kernel(const StepArgs a)
 }
 
 
-template <int MODE, class S, bool REC = false>
+template <int MODE, class S, bool REC = false, bool MU = false>
 cudaError_t launch_cell(StepArgs a, cudaStream_t s)
 {
     a.nblk_x = (a.nx + kBX - 1) / kBX;
@@ -620,7 +640,8 @@ cudaError_t launch_cell(StepArgs a, cudaStream_t s)
     a.nblk_main = a.nblk_x * ((a.ny * a.nz + a.rows_per_block - 1) / a.rows_per_block);
     if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
     if (REC && a.rec == nullptr) return cudaErrorInvalidValue;
-    step_kernel_cell<MODE, S, kBX, REC><<<a.nblk_main, kBX, 0, s>>>(a);
+    if (MU && a.inv_mu == nullptr) return cudaErrorInvalidValue;
+    step_kernel_cell<MODE, S, kBX, REC, MU><<<a.nblk_main, kBX, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -685,6 +706,22 @@ cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s
     case 6: return launch_cell<2, float>(a, s);
     case 7: return launch_cell<2, __half>(a, s);
     case 8: return launch_cell<2, __nv_bfloat16>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_t s)
+{
+    switch (mode * 3 + storage) {
+    case 0: return launch_cell<0, float, false, true>(a, s);
+    case 1: return launch_cell<0, __half, false, true>(a, s);
+    case 2: return launch_cell<0, __nv_bfloat16, false, true>(a, s);
+    case 3: return launch_cell<1, float, false, true>(a, s);
+    case 4: return launch_cell<1, __half, false, true>(a, s);
+    case 5: return launch_cell<1, __nv_bfloat16, false, true>(a, s);
+    case 6: return launch_cell<2, float, false, true>(a, s);
+    case 7: return launch_cell<2, __half, false, true>(a, s);
+    case 8: return launch_cell<2, __nv_bfloat16, false, true>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -67,6 +67,7 @@ _SIGS = {
     "lbem_create": (_I32, [ctypes.POINTER(GridDesc), _I32, _P, _I32, _P, _P, ctypes.c_size_t,
                            ctypes.POINTER(_P)]),
     "lbem_set_permittivity": (_I32, [_P, _P, _I32]),
+    "lbem_set_permeability": (_I32, [_P, _P, _I32]),
     "lbem_inject_plane_wave": (_I32, [_P, ctypes.POINTER(PlaneWaveDesc)]),
     "lbem_set_dft_window": (_I32, [_P, _I64, _I32]),
     "lbem_step": (_I32, [_P, _I64]),
@@ -188,6 +189,12 @@ def lbem_create(grid: GridDesc, eps_r, stream=None, workspace=None) -> int:
 def lbem_set_permittivity(h, eps_r):
     ep, on_dev = _ptr(eps_r)
     _check(lib().lbem_set_permittivity(h, ep, on_dev), h)
+
+
+def lbem_set_permeability(h, mu_r):
+    """mu_r: float32 [nz][ny][nx] (host or CUDA) or None for mu_r = 1."""
+    mp, on_dev = _ptr(mu_r)
+    _check(lib().lbem_set_permeability(h, mp, on_dev), h)
 
 
 def lbem_inject_plane_wave(h, wave: PlaneWaveDesc):
@@ -484,6 +491,10 @@ class Solver:
     def set_permittivity(self, eps):
         lbem_set_permittivity(self.h, eps if hasattr(eps, "data_ptr") else
                               np.ascontiguousarray(eps, np.float32))
+
+    def set_permeability(self, mu):
+        lbem_set_permeability(self.h, None if mu is None else (
+            mu if hasattr(mu, "data_ptr") else np.ascontiguousarray(mu, np.float32)))
 
     def set_dft_window(self, t_start, n_periods=1):
         lbem_set_dft_window(self.h, t_start, n_periods)

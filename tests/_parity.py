@@ -72,6 +72,8 @@ def gpu_solver(problem, storage="f32", init=None, steps=None, dft=True):
     from paper_2510_11042_gb300 import lbem
     s = lbem.Solver(problem.shape, problem.eps, problem.mode, storage, problem.absorber_width,
                     problem.sigma_max)
+    if getattr(problem, "mu", None) is not None:
+        s.set_permeability(problem.mu)
     if init is not None:
         s.set_populations(init)
     if problem.wave is not None:

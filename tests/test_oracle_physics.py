@@ -10,6 +10,7 @@
   * Mie series vs the min/max printed in Tables 1 and 5;
   * the whole pipeline on a small cylinder vs Lorenz-Mie (Sec. 3.2), with mirror symmetry.
 """
+import dataclasses
 import math
 import os
 
@@ -51,23 +52,29 @@ def test_vacuum_phase_speed_is_one_third_second_order():
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
 
 
-@pytest.mark.parametrize("eps_r", [2.25, 10.0, 40.0])
-def test_fresnel_normal_incidence(eps_r):
-    lam = round(3 * 20 * math.sqrt(eps_r)) / 3.0   # lambda_wall / dx = 20 (Sec. 3.1)
+@pytest.mark.parametrize("eps_r,mu_r", [(2.25, 1.0), (10.0, 1.0), (40.0, 1.0), (1.0, 4.0), (4.0, 4.0),
+                                         (9.0, 4.0), (200.0, 1.0), (1.0, 200.0)])
+def test_fresnel_normal_incidence(eps_r, mu_r):
+    """Eq. 11 at a planar wall, including magnetic media (the paper's 1D sweep
+    over eps_r, mu_r in [1, 200], Sec. 3.1), at lambda_wall / dx = 20."""
+    n_wall = math.sqrt(eps_r * mu_r)
+    lam = round(3 * 20 * n_wall) / 3.0
     n = int(10 * lam)
     xi = n // 2
     eps = np.ones((1, 1, n), np.float32)
     eps[..., xi:] = eps_r
-    p = line_problem(lam, n, eps=eps,
-                     periods=int(math.ceil(2 * n * math.sqrt(eps_r) / (3 * lam))) + 8)
+    mu = np.ones((1, 1, n), np.float32)
+    mu[..., xi:] = mu_r
+    p = line_problem(lam, n, eps=eps, periods=int(math.ceil(2 * n * n_wall / (3 * lam))) + 8)
+    p = dataclasses.replace(p, mu=mu)
     r = lb.Run(p).run()
     z = r.phasors()[0, 0, :, 2]
     e_i = r.incident_amplitude()
     xs = np.arange(n)
     refl = np.abs(z[(xs > 22) & (xs < p.wave.tf_lo[0] - 1)]).mean() / e_i
-    trans = np.abs(z[(xs >= xi) & (xs < xi + 2 * lam / math.sqrt(eps_r))]).mean() / e_i
-    r_ex, t_ex = fresnel.normal_incidence(eps_r)
-    assert refl == pytest.approx(abs(r_ex), rel=0.02)
+    trans = np.abs(z[(xs >= xi) & (xs < xi + 2 * lam / n_wall)]).mean() / e_i
+    r_ex, t_ex = fresnel.normal_incidence(eps_r, mu_r)
+    assert abs(refl - abs(r_ex)) <= 0.02 * abs(r_ex) + 2e-3, (refl, r_ex)
     assert trans == pytest.approx(t_ex, rel=0.02)
 
 

@@ -70,6 +70,7 @@ class Problem:
     steps: int
     dft_periods: int = 1
     meta: dict = field(default_factory=dict)
+    mu: Optional[np.ndarray] = None      # float32 [nz][ny][nx] relative permeability, None: 1
 
     @property
     def period(self) -> int:
