@@ -106,7 +106,22 @@ typedef struct {
  * population of the link's source cell.  The NTFF box [ntff_lo, ntff_hi] must
  * enclose the total-field box strictly and lie outside the absorbing layer;
  * center is the phase reference of the far field.  For 2D grids the z entries
- * of the boxes must be 0. */
+ * of the boxes must be 0.
+ *
+ * source_kind = LBEM_SOURCE_ANALYTIC instead takes the incident populations
+ * from the closed-form plane wave: the vacuum equilibrium (Eq. 2) of
+ * E = amplitude * ramp(tau) * sin(w tau) * pol, H = dir x E at the link's
+ * source cell r and time n, tau = n - 3 dir.(r - origin) (c = 1/3, Eq. 3).  dir
+ * may then be any unit vector (in the xy plane for the 2D modes), and the
+ * total-field box may extend past the grid (a one-sided box, e.g. the
+ * half-space x >= x_s) and into the absorbing layer.  An NTFF box is then
+ * optional: all-zero ntff bounds mean none (no DFT, no far field), otherwise
+ * the rules above apply and |E_I| of Eqs. 5-6 is the amplitude.  The
+ * analytic wave is not an exact solution of the discrete scheme, so every
+ * cell of the total-field box carries a source term; the line source is
+ * exact and costs nothing outside dielectric cells. */
+#define LBEM_SOURCE_LINE 0
+#define LBEM_SOURCE_ANALYTIC 1
 typedef struct {
     double dir[3];
     double pol[3];
@@ -117,6 +132,8 @@ typedef struct {
     int32_t ntff_lo[3], ntff_hi[3];
     double center[3];
     int32_t source_index;
+    int32_t source_kind;   /* LBEM_SOURCE_LINE or LBEM_SOURCE_ANALYTIC */
+    double origin[3];      /* analytic source: where tau = n */
 } lbem_plane_wave;
 
 /* Bytes of device workspace a grid needs (populations in two buffers, the

@@ -294,6 +294,19 @@ class Run:
         if abs(3 * w.wavelength - self.T) > 1e-9:
             raise ValueError("3*wavelength must be an integer (the period in steps)")
         self.omega = 2 * math.pi / self.T
+        self.dft_t0 = problem.dft_start
+        self.dft_P = problem.dft_periods
+        self.k_hat = np.asarray(w.direction, float)
+        self.pol = np.asarray(w.polarization, float)
+        self.t_ramp = w.ramp_periods * self.T
+        if getattr(w, "analytic", False):
+            # closed-form source: vacuum equilibrium of the plane wave at the link's source cell
+            self.line = None
+            self.main.set_tfsf_analytic(w.tf_lo, w.tf_hi, self.k_hat, self.pol, w.amplitude,
+                                        self.omega, self.t_ramp, w.origin)
+            if record_dft:
+                self.main.enable_dft()
+            return
         self.axis = _axis_of(w.direction)
         if self.axis is None:
             raise ValueError("the incident line needs an axis-aligned direction")
@@ -334,6 +347,10 @@ class Run:
             n = self.t
             t = n + 1
             dft = self._dft_args(t)
+            if self.line is None:
+                self.main.step(n, dft=dft)
+                self.t = t
+                continue
             inc = self.line.f  # incident post-collision populations at time n
             self.main.step(n, inc_line=inc, dft=dft)
             E, H = self.incident_fields(t)
@@ -359,7 +376,10 @@ class Run:
 
     def incident_amplitude(self):
         """|E^I| (Eq. 5/6): magnitude of the incident line's E phasor along p_hat,
-        averaged over the two nodes bracketing the far-field centre (reading)."""
+        averaged over the two nodes bracketing the far-field centre (reading); the
+        amplitude itself for the closed-form source."""
+        if self.line is None:
+            return float(self.problem.wave.amplitude)
         zl = self.line_phasors()[:, :3] @ self.pol
         c = self.problem.wave.center[self.axis]
         i0 = int(math.floor(c))

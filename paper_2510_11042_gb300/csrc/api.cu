@@ -29,8 +29,10 @@ struct lbem_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     float *inv_eps = nullptr;
-    float *inv_mu = nullptr;    // 1/mu_r plane; used only when mu_on
+    float *inv_mu = nullptr;    // 1/mu_r plane (1 where no map is set); read when mu_on or analytic
     bool mu_on = false;
+    bool analytic = false;      // the plane wave is the closed-form source, not the line
+    PlaneWaveA pw;
     float *line[3] = {nullptr, nullptr, nullptr};  // incident line at t, t+1, t+2 (mod 3)
     int n_line_max = 0;
     double *dft = nullptr;
@@ -204,11 +206,15 @@ static IncView inc_view(lbem_ctx *h)
     IncView v;
     std::memset(&v, 0, sizeof v);
     if (!h->has_wave) return v;
-    v.on = 1;
+    v.on = h->analytic ? 2 : 1;
     for (int k = 0; k < 3; ++k) {
         v.tf_lo[k] = h->wave.tfsf_lo[k];
         v.tf_hi[k] = h->wave.tfsf_hi[k];
     }
+    v.mode = h->g.mode;
+    v.pw = h->pw;
+    v.t = (double)h->t;
+    if (h->analytic) return v;
     v.axis = h->inc_axis;
     v.line = line_at(h, h->t);
     v.n = h->n_line;
@@ -229,8 +235,10 @@ static void fill_common_args(lbem_ctx *h, StepArgs &a)
     a.inv_scale = h->inv_scale;
     a.status = h->flag + 1;
     if (!h->has_wave) return;
-    a.tfsf = 1;
-    a.line_on = 1;
+    a.tfsf = h->analytic ? 2 : 1;
+    a.line_on = h->analytic ? 0 : 1;
+    a.pw = h->pw;
+    if (h->analytic) a.inv_mu = h->inv_mu;
     for (int k = 0; k < 3; ++k) {
         a.tf_lo[k] = h->wave.tfsf_lo[k];
         a.tf_hi[k] = h->wave.tfsf_hi[k];
@@ -352,6 +360,7 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, (size_t)L.Q * L.P * L.elem, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, (size_t)L.Q * L.P * L.elem, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->inv_eps, 0, (size_t)L.P * 4, h->stream);
+    if (e == cudaSuccess) e = launch_fill(h->inv_mu, L.P, 1.0f, h->stream);
     if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaMemsetAsync");
     if (rc == LBEM_OK) rc = upload_eps(h, eps_r, eps_on_device);
     if (rc != LBEM_OK) {
@@ -377,6 +386,7 @@ int32_t lbem_set_permeability(lbem_handle h, const float *mu_r, int32_t mu_on_de
     h->adj_valid = false;
     if (!mu_r) {
         h->mu_on = false;
+        CK(h, launch_fill(h->inv_mu, h->P, 1.0f, h->stream));
         return LBEM_OK;
     }
     const int rc = upload_inverse(h, mu_r, mu_on_device, h->inv_mu, "mu_r");
@@ -427,10 +437,14 @@ static void build_faces(lbem_ctx *h)
     h->dft_doubles = (size_t)off;
 }
 
+static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w);
+
 int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
 {
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
     if (!w) return fail(h, LBEM_ERR_ARG, "wave is NULL");
+    if (w->source_kind == LBEM_SOURCE_ANALYTIC) return inject_analytic(h, w);
+    if (w->source_kind != LBEM_SOURCE_LINE) return fail(h, LBEM_ERR_ARG, "unknown source_kind %d", w->source_kind);
     const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
     const int ax = axis_of(w->dir);
     if (ax < 0) return fail(h, LBEM_ERR_ARG, "dir must be +x, +y or +z");
@@ -478,6 +492,8 @@ int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
     h->wave = *w;
     h->wave.source_index = src;
     h->has_wave = true;
+    h->analytic = false;
+    std::memset(&h->pw, 0, sizeof h->pw);
     h->T = (int)std::lround(T);
     h->omega = 2.0 * M_PI / h->T;
     h->inc_axis = ax;
@@ -497,6 +513,89 @@ int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
     a.line_out = line_at(h, h->t + 1);
     source_fields(h, h->t + 1, a.src_E, a.src_H);
     CK(h, launch_line_init(h->g.mode, a, h->stream));
+    h->launches += 1;
+    return LBEM_OK;
+}
+
+// The closed-form plane-wave source (see lbem_plane_wave).
+static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w)
+{
+    const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
+    double dn = 0, pn = 0, pd = 0;
+    for (int a = 0; a < 3; ++a) {
+        dn += w->dir[a] * w->dir[a];
+        pn += w->pol[a] * w->pol[a];
+        pd += w->pol[a] * w->dir[a];
+    }
+    if (std::fabs(dn - 1.0) > 1e-9 || std::fabs(pn - 1.0) > 1e-9 || std::fabs(pd) > 1e-9)
+        return fail(h, LBEM_ERR_ARG, "dir and pol must be orthogonal unit vectors");
+    if (h->g.mode != 2 && std::fabs(w->dir[2]) > 1e-12)
+        return fail(h, LBEM_ERR_ARG, "2D modes need dir in the xy plane");
+    if (h->g.mode == 0 && (std::fabs(w->pol[0]) > 1e-12 || std::fabs(w->pol[1]) > 1e-12))
+        return fail(h, LBEM_ERR_ARG, "EZ mode needs pol along z");
+    if (h->g.mode == 1 && std::fabs(w->pol[2]) > 1e-12)
+        return fail(h, LBEM_ERR_ARG, "HZ mode needs pol in the xy plane");
+    const double T = 3.0 * w->wavelength;
+    if (!(w->wavelength > 0) || std::fabs(T - std::round(T)) > 1e-9 || std::round(T) < 2)
+        return fail(h, LBEM_ERR_ARG, "3*wavelength must be an integer >= 2 (the period in steps)");
+    if (!(w->amplitude > 0) || !std::isfinite(w->amplitude))
+        return fail(h, LBEM_ERR_ARG, "amplitude must be positive");
+    if (!(w->ramp_periods >= 0)) return fail(h, LBEM_ERR_ARG, "ramp_periods must be >= 0");
+    bool ntff = false;
+    for (int a = 0; a < 3; ++a) ntff = ntff || w->ntff_lo[a] || w->ntff_hi[a];
+    const int W = h->g.absorber_width;
+    for (int a = 0; a < 3; ++a) {
+        if (w->tfsf_lo[a] > w->tfsf_hi[a]) return fail(h, LBEM_ERR_ARG, "axis %d: tfsf_lo > tfsf_hi", a);
+        if (n3[a] == 1) {
+            if (w->ntff_lo[a] || w->ntff_hi[a])
+                return fail(h, LBEM_ERR_ARG, "NTFF bounds along a 1-cell axis must be 0");
+            continue;
+        }
+        if (ntff && !(W <= w->ntff_lo[a] && w->ntff_lo[a] < w->tfsf_lo[a] && w->tfsf_hi[a] < w->ntff_hi[a] &&
+                      w->ntff_hi[a] <= n3[a] - 1 - W))
+            return fail(h, LBEM_ERR_ARG,
+                        "axis %d: an NTFF box needs W <= ntff_lo < tfsf_lo <= tfsf_hi < ntff_hi <= n-1-W", a);
+    }
+    if (h->has_wave) {
+        CK(h, launch_add_incident(h->g.mode, h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx,
+                                  h->g.ny, h->g.nz, h->nxp, inc_view(h), 1.0f, h->stream));
+        h->launches += 1;
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    h->adj_valid = false;
+    h->wave = *w;
+    h->has_wave = true;
+    h->analytic = true;
+    h->T = (int)std::lround(T);
+    h->omega = 2.0 * M_PI / h->T;
+    h->inc_axis = 0;
+    h->n_line = 1;
+    h->src_index = 0;
+    PlaneWaveA &p = h->pw;
+    for (int a = 0; a < 3; ++a) {
+        p.k[a] = w->dir[a];
+        p.pol[a] = w->pol[a];
+        p.r0[a] = w->origin[a];
+    }
+    p.kxp[0] = w->dir[1] * w->pol[2] - w->dir[2] * w->pol[1];
+    p.kxp[1] = w->dir[2] * w->pol[0] - w->dir[0] * w->pol[2];
+    p.kxp[2] = w->dir[0] * w->pol[1] - w->dir[1] * w->pol[0];
+    p.amp = w->amplitude;
+    p.omega = h->omega;
+    p.t_ramp = w->ramp_periods * h->T;
+    if (ntff) {
+        build_faces(h);
+    } else {
+        h->faces.nfaces = 0;
+        h->faces.cell_start[0] = 0;
+        h->dft_doubles = 0;
+    }
+    h->dft_t0 = -1;
+    h->dft_periods = 0;
+    if (h->dft_doubles) CK(h, cudaMemsetAsync(h->dft, 0, h->dft_doubles * 8, h->stream));
+    // the stored state holds scattered parts inside the new box
+    CK(h, launch_add_incident(h->g.mode, h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx, h->g.ny,
+                              h->g.nz, h->nxp, inc_view(h), -1.0f, h->stream));
     h->launches += 1;
     return LBEM_OK;
 }
@@ -528,11 +627,15 @@ int32_t lbem_step(lbem_handle h, int64_t n)
             a.fout_q[q] = (char *)h->f[h->cur ^ 1] + q * plane_bytes;
         }
         if (h->has_wave) {
-            a.line_n = line_at(h, h->t);
-            a.line_n1 = line_at(h, h->t + 1);
-            a.line_out = line_at(h, h->t + 2);
-            source_fields(h, h->t + 2, a.src_E, a.src_H);
-            a.dft_on = (h->dft_t0 >= 1 && t >= h->dft_t0 && t < h->dft_t0 + (int64_t)h->dft_periods * h->T);
+            if (!h->analytic) {
+                a.line_n = line_at(h, h->t);
+                a.line_n1 = line_at(h, h->t + 1);
+                a.line_out = line_at(h, h->t + 2);
+                source_fields(h, h->t + 2, a.src_E, a.src_H);
+            }
+            a.tn = h->t;
+            a.dft_on = (h->faces.nfaces > 0 && h->dft_t0 >= 1 && t >= h->dft_t0 &&
+                        t < h->dft_t0 + (int64_t)h->dft_periods * h->T);
             if (a.dft_on) {
                 const double ph = 2.0 * M_PI * (double)(t % h->T) / (double)h->T;
                 a.dft_c = std::cos(ph);
@@ -541,8 +644,9 @@ int32_t lbem_step(lbem_handle h, int64_t n)
                 a.dft_scale_cells = a.dft_scale * h->scale;            // lattice (storage units)
             }
         }
-        cudaError_t e = h->mu_on ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
-                                 : launch_step(h->g.mode, h->g.storage, a, h->stream);
+        cudaError_t e = h->analytic ? launch_step_analytic(h->g.mode, h->g.storage, a, h->stream)
+                        : h->mu_on  ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
+                                    : launch_step(h->g.mode, h->g.storage, a, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
         h->launches += 1;
         h->cur ^= 1;
@@ -610,6 +714,8 @@ extern "C" int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, 
             return bfail(nullptr, LBEM_ERR_ARG, "all handles of a batch need the same mode and storage");
         if (handles[i]->mu_on)
             return bfail(nullptr, LBEM_ERR_ARG, "batched runs support mu_r = 1 only");
+        if (handles[i]->analytic)
+            return bfail(nullptr, LBEM_ERR_ARG, "batched runs need the incident-line source");
         if (handles[i]->device != dev) return bfail(nullptr, LBEM_ERR_ARG, "handle %d is on another device", i);
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return bfail(nullptr, LBEM_ERR_ARG, "handle %d repeated", i);
@@ -828,8 +934,10 @@ int32_t lbem_far_field(lbem_handle h, const double *theta, const double *phi, in
     if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
     if (n < 0 || (n > 0 && (!theta || !s2))) return fail(h, LBEM_ERR_ARG, "bad angle arrays");
     if (h->g.mode == 2 && n > 0 && !phi) return fail(h, LBEM_ERR_ARG, "3D needs phi");
+    if (h->faces.nfaces == 0) return fail(h, LBEM_ERR_STATE, "the plane wave has no NTFF box");
     FarFieldArgs a;
     std::memset(&a, 0, sizeof a);
+    a.ei_fixed = h->analytic ? h->wave.amplitude : 0.0;
     a.dft = h->dft;
     a.line_dft = h->line_dft;
     a.g = h->faces;
@@ -875,6 +983,10 @@ int32_t lbem_incident_amplitude(lbem_handle h, double *out)
 {
     if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
     if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
+    if (h->analytic) {
+        *out = h->wave.amplitude;
+        return LBEM_OK;
+    }
     int i0, i1;
     centre_nodes(h, &i0, &i1);
     double v[2][6];
@@ -1157,6 +1269,7 @@ int32_t lbem_forward_checkpointed(lbem_handle h, int64_t n_steps, int32_t K, voi
     if (n_steps < 1 || K < 1) return fail(h, LBEM_ERR_ARG, "need n_steps >= 1 and K >= 1");
     if (h->g.storage != LBEM_F32) return fail(h, LBEM_ERR_ARG, "the adjoint needs FP32 storage");
     if (h->mu_on) return fail(h, LBEM_ERR_ARG, "the adjoint supports mu_r = 1 only");
+    if (h->analytic) return fail(h, LBEM_ERR_ARG, "the adjoint needs the incident-line source");
     if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
     if (h->t != 0) return fail(h, LBEM_ERR_STATE, "the checkpointed run must start at t = 0 (got t = %lld)",
                                (long long)h->t);

@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -150,6 +151,26 @@ __host__ __device__ constexpr int slot_H(int mode, int c)
     return mode == 0 ? (c < 2 ? 1 + c : -1) : (mode == 1 ? (c == 2 ? 2 : -1) : 3 + c);
 }
 
+// Closed-form incident plane wave (analytic TF/SF source):
+//   tau = t - 3 k.(p - r0),  s = amp ramp(tau) sin(omega tau),  E = s pol, H = s kxp,
+// ramp(tau) = (1 - cos(pi tau / t_ramp)) / 2 on 0 < tau < t_ramp (0 before, 1 after).
+struct PlaneWaveA {
+    double k[3], pol[3], kxp[3];
+    double amp, omega, t_ramp;
+    double r0[3];
+};
+
+__device__ __forceinline__ double pw_amplitude(const PlaneWaveA &w, double px, double py, double pz,
+                                               double t)
+{
+    const double tau = t - 3.0 * (w.k[0] * (px - w.r0[0]) + w.k[1] * (py - w.r0[1]) +
+                                  w.k[2] * (pz - w.r0[2]));
+    double ramp = 1.0;
+    if (tau <= 0.0) ramp = 0.0;
+    else if (tau < w.t_ramp) ramp = 0.5 * (1.0 - cos(M_PI * tau / w.t_ramp));
+    return w.amp * ramp * sin(w.omega * tau);
+}
+
 // Arguments of the fused step kernel (passed by value).
 struct StepArgs {
     const void *fin_q[kMaxQ];  // start of each input population plane
@@ -165,9 +186,12 @@ struct StepArgs {
     // absorbing layer
     int w;
     float sigma_max, inv_w;
-    // TF/SF source: the incident line at time n+1 ([Q][n_line]); line_n is
-    // used only to start a fresh line
+    // TF/SF source: 1 = the incident line at time n+1 ([Q][n_line]; line_n is
+    // used only to start a fresh line), 2 = the analytic plane wave pw at the
+    // input state's time tn
     int tfsf;
+    PlaneWaveA pw;
+    long long tn;
     int tf_lo[3], tf_hi[3];
     int inc_axis;
     const float *line_n;
@@ -232,6 +256,9 @@ int batch_max_blocks_per_sm(int mode, int storage);
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
 // The step kernel with a per-cell mu_r (a.inv_mu), Eq. 2's h_0 = (mu_r - 1) H
 cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_t s);
+// The step kernel with the analytic plane-wave source (a.tfsf == 2; reads a.inv_mu)
+cudaError_t launch_step_analytic(int mode, int storage, const StepArgs &a, cudaStream_t s);
+cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 cudaError_t launch_line_init(int mode, const StepArgs &a, cudaStream_t s);
 // The step kernel with a.rec written (FP32 storage; forward replay of the adjoint)
 cudaError_t launch_step_record(int mode, const StepArgs &a, cudaStream_t s);
@@ -239,11 +266,14 @@ cudaError_t launch_step_record(int mode, const StepArgs &a, cudaStream_t s);
 // Where the stored populations hold the scattered part G = F - I (inside the
 // total-field box), diagnostics add the incident line back.
 struct IncView {
-    int on;
+    int on;                    // 1: incident line, 2: analytic plane wave
     int tf_lo[3], tf_hi[3];
     int axis;
     const float *line;         // incident line at the state's time, [Q][n]
     int n;
+    int mode;                  // analytic: population planes of this mode
+    PlaneWaveA pw;
+    double t;                  // analytic: the state's time
 };
 
 // Observables and data movement (observe.cu)
@@ -267,6 +297,7 @@ struct FarFieldArgs {
     double center[3];
     double pol[3];
     int center_i0, center_i1;  // incident-line nodes bracketing the centre
+    double ei_fixed;           // > 0: |E_I| given (analytic source) instead of the line's DFT
     int chunks;
     double *partial;           // [n_ang][chunks][12]
     double *s2;                // [n_ang]

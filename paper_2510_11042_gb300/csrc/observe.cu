@@ -183,7 +183,7 @@ __global__ void far_field_finalize(const FarFieldArgs a)
     // |E_I|: incident-line E phasor along pol, mean over the two nodes around the centre
     double ei = 0.0;
     const int nodes[2] = {a.center_i0, a.center_i1};
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < 2 && a.ei_fixed <= 0.0; ++t) {
         double re = 0.0, im = 0.0;
         for (int c = 0; c < 3; ++c) {
             re += a.pol[c] * a.line_dft[(nodes[t] * 3 + c) * 2 + 0];
@@ -191,6 +191,7 @@ __global__ void far_field_finalize(const FarFieldArgs a)
         }
         ei += 0.5 * sqrt(re * re + im * im);
     }
+    if (a.ei_fixed > 0.0) ei = a.ei_fixed;
     const double th = a.theta[ang];
     const double k = a.k;
     double s2;
@@ -256,8 +257,26 @@ __device__ __forceinline__ float inc_at(const IncView &v, int q, int x, int y, i
     if (x < v.tf_lo[0] || x > v.tf_hi[0] || y < v.tf_lo[1] || y > v.tf_hi[1] || z < v.tf_lo[2] ||
         z > v.tf_hi[2])
         return 0.f;
+    if (v.on == 2) {
+        // vacuum equilibrium (Eq. 2) of the analytic plane wave at the state's time
+        const int i = plane_dir(v.mode, q), s = plane_slot(v.mode, q);
+        if (i == 0) return 0.f;
+        const int ne = mode_NE(v.mode);
+        const int c = s < ne ? (v.mode == 0 ? 2 : s) : (v.mode == 1 ? 2 : s - ne);
+        const float amp = (float)pw_amplitude(v.pw, x, y, z, v.t);
+        const float E[3] = {amp * (float)v.pw.pol[0], amp * (float)v.pw.pol[1], amp * (float)v.pw.pol[2]};
+        const float H[3] = {amp * (float)v.pw.kxp[0], amp * (float)v.pw.kxp[1], amp * (float)v.pw.kxp[2]};
+        return s < ne ? (E[c] - cross_c(i, H, c)) * (1.0f / 6.0f) : (H[c] + cross_c(i, E, c)) * (1.0f / 6.0f);
+    }
     const int s = v.axis == 0 ? x : (v.axis == 1 ? y : z);
     return v.line[(size_t)q * v.n + s];
+}
+
+__global__ void fill_kernel(float *p, long long n, float v)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
 }
 
 // Plane q of the stored populations: element base + w * cell (pop_index).
@@ -440,6 +459,12 @@ cudaError_t launch_far_field_partial(const FarFieldArgs &a, cudaStream_t s)
     case 5: LBEM_FF_TABLES(2); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s)
+{
+    fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
     return cudaGetLastError();
 }
 

@@ -166,6 +166,70 @@ __device__ __forceinline__ void line_work(const StepArgs &a, int s)
                     a.inc_axis);
 }
 
+// Analytic TF/SF source of a cell inside the total-field box, in storage
+// units: keep * C(I_pulled) - I(r, n+1), where I(p, t) is the vacuum
+// equilibrium (Eq. 2) of the closed-form plane wave at cell p and time t, and
+// I_pulled takes direction i's populations from the cell the clamped pull
+// reads, clamp(r - c_i), at time n.  (Storing G = F - I inside the box, the
+// link-wise rule F_pulled = G_pulled + chi(r) I_pulled makes
+// G* = keep C(G_pulled) + chi(r) [keep C(I_pulled) - I(r, n+1)].)
+template <int MODE>
+__device__ __forceinline__ void analytic_source(const StepArgs &a, int x, int y, int z, float inv_eps,
+                                                float inv_mu, float keep, float *src)
+{
+    using PL = Planes<MODE>;
+    constexpr int Q = PL::Q;
+    constexpr float sixth = 1.0f / 6.0f;
+    const double t = (double)a.tn;
+    const float pol[3] = {(float)a.pw.pol[0], (float)a.pw.pol[1], (float)a.pw.pol[2]};
+    const float kxp[3] = {(float)a.pw.kxp[0], (float)a.pw.kxp[1], (float)a.pw.kxp[2]};
+    float amp[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const int d = dir_axis(i), sg = dir_sign(i);
+        const int px = min(max(x - (d == 0 ? sg : 0), 0), a.nx - 1);
+        const int py = min(max(y - (d == 1 ? sg : 0), 0), a.ny - 1);
+        const int pz = min(max(z - (d == 2 ? sg : 0), 0), a.nz - 1);
+        amp[i] = (float)pw_amplitude(a.pw, px, py, pz, t);
+    }
+    float D[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int i = PL::dir(q), c = PL::comp(q);
+        const float E[3] = {amp[i] * pol[0], amp[i] * pol[1], amp[i] * pol[2]};
+        const float H[3] = {amp[i] * kxp[0], amp[i] * kxp[1], amp[i] * kxp[2]};
+        float v = 0.f;
+        if (i != 0) v = PL::fam(q) == 0 ? (E[c] - cross_c(i, H, c)) * sixth : (H[c] + cross_c(i, E, c)) * sixth;
+        src[q] = v;
+        if (PL::fam(q) == 0) D[c] += v;
+        else B[c] += v;
+    }
+    float E[3], H[3], E3[3], H3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        E[c] = D[c] * inv_eps;
+        H[c] = B[c] * inv_mu;
+        E3[c] = third(E[c]);
+        H3[c] = third(H[c]);
+    }
+    const float an = (float)pw_amplitude(a.pw, x, y, z, t + 1.0);
+    const float En[3] = {an * pol[0], an * pol[1], an * pol[2]};
+    const float Hn[3] = {an * kxp[0], an * kxp[1], an * kxp[2]};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int i = PL::dir(q), c = PL::comp(q);
+        float eq2, In = 0.f;
+        if (PL::fam(q) == 0) {
+            eq2 = (i == 0) ? 2.f * (D[c] - E[c]) : E3[c] - cross_c(i, H3, c);
+            if (i != 0) In = (En[c] - cross_c(i, Hn, c)) * sixth;
+        } else {
+            eq2 = (i == 0) ? 2.f * (B[c] - H[c]) : H3[c] + cross_c(i, E3, c);
+            if (i != 0) In = (Hn[c] + cross_c(i, En, c)) * sixth;
+        }
+        src[q] = (keep * (eq2 - src[q]) - In) * a.inv_scale;
+    }
+}
+
 // Accessor of one cell's pulled populations held in registers.
 struct FloatCell {
     float *f;
@@ -179,7 +243,7 @@ struct FloatCell {
 // Values are in storage units (population / scale); fields go to the DFT
 // multiplied back by the scale (dft_scale_cells), the incident source is
 // divided by it.
-template <int MODE, bool REC = false, bool MU = false, class Cell>
+template <int MODE, bool REC = false, bool MU = false, bool ANA = false, class Cell>
 __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float inv_eps,
                                             const StepArgs &a, float inv_mu = 1.0f)
 {
@@ -255,9 +319,10 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
     // incident-field source of dielectric cells inside the total-field box
     // (the box lies outside the absorbing layer, so keep == 1 there)
     // (with magnetic media also the field dH = H_inc (1/mu_r - 1))
-    const bool source = a.tfsf && (inv_eps != 1.0f || (MU && inv_mu != 1.0f)) &&
+    const bool source = a.tfsf == 1 && (inv_eps != 1.0f || (MU && inv_mu != 1.0f)) &&
                         in_box(x, y, z, a.tf_lo, a.tf_hi);
-    if (!source && keep == 1.0f) {
+    const bool ana = ANA && in_box(x, y, z, a.tf_lo, a.tf_hi);
+    if (!source && !ana && keep == 1.0f) {
         // most cells: plain collision, f* = 2 f_eq - f
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -269,6 +334,8 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
         }
         return;
     }
+    float asrc[ANA ? Q : 1];
+    if (ANA && ana) analytic_source<MODE>(a, x, y, z, inv_eps, inv_mu, keep, asrc);
     float dE[3] = {0.f, 0.f, 0.f}, dE3[3] = {0.f, 0.f, 0.f};
     float dH[3] = {0.f, 0.f, 0.f}, dH3[3] = {0.f, 0.f, 0.f};
     if (source) {
@@ -307,7 +374,11 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
             src = (i == 0) ? (MU ? -2.f * dH[ac] : 0.f)
                            : (MU ? dH3[ac] + cross_c(i, dE3, ac) : cross_c(i, dE3, ac));
         }
-        f.set(q, (eq2 - f.get(q) + src) * keep);
+        float v = (eq2 - f.get(q) + src) * keep;
+        if constexpr (ANA) {
+            if (ana) v += asrc[q];
+        }
+        f.set(q, v);
     }
 }
 
@@ -438,7 +509,7 @@ __device__ __forceinline__ void store_cell(const StepArgs &a, int c, const float
 // in-group offset from a constant-bank base; the +-x pulls are plain loads
 // shifted by one element (coalesced; the extra sector per warp hits in L1/L2).
 // The cells x = bx * BX + threadIdx.x of row (y, z) for one step.
-template <int MODE, class S, int BX, bool REC = false, bool MU = false>
+template <int MODE, class S, int BX, bool REC = false, bool MU = false, bool ANA = false>
 __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int z)
 {
     using PL = Planes<MODE>;
@@ -460,8 +531,8 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
     float f[Q];
     load_cell<MODE, S>(a, src, f);
     FloatCell cell{f};
-    update_cell<MODE, REC, MU>(cell, x, y, z, __ldg(a.inv_eps + c), a,
-                               MU ? __ldg(a.inv_mu + c) : 1.0f);
+    update_cell<MODE, REC, MU, ANA>(cell, x, y, z, __ldg(a.inv_eps + c), a,
+                                    MU ? __ldg(a.inv_mu + c) : 1.0f);
     store_cell<MODE, S>(a, c, f);
 }
 
@@ -472,7 +543,7 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
 // chosen by timing the 384^3 sphere on GB300.
 template <class S> __host__ __device__ constexpr int rows_of() { return sizeof(S) == 4 ? 2 : 4; }
 
-template <int MODE, class S, int BX, bool REC = false, bool MU = false>
+template <int MODE, class S, int BX, bool REC = false, bool MU = false, bool ANA = false>
 __global__ void __launch_bounds__(BX, 7) step_kernel_cell(const StepArgs a)
 {
     constexpr int R = rows_of<S>();
@@ -484,7 +555,7 @@ __global__ void __launch_bounds__(BX, 7) step_kernel_cell(const StepArgs a)
     const int bx = b % a.nblk_x;
     const int r0 = (b / a.nblk_x) * R;
     const int r1 = min(r0 + R, a.ny * a.nz);
-    for (int r = r0; r < r1; ++r) row_cells<MODE, S, BX, REC, MU>(a, bx, r % a.ny, r / a.ny);
+    for (int r = r0; r < r1; ++r) row_cells<MODE, S, BX, REC, MU, ANA>(a, bx, r % a.ny, r / a.ny);
 }
 
 constexpr int kBX = 128;  // threads per block = cells per row tile
@@ -632,7 +703,7 @@ __global__ void line_init_kernel(const StepArgs a)
 }
 
 
-template <int MODE, class S, bool REC = false, bool MU = false>
+template <int MODE, class S, bool REC = false, bool MU = false, bool ANA = false>
 cudaError_t launch_cell(StepArgs a, cudaStream_t s)
 {
     a.nblk_x = (a.nx + kBX - 1) / kBX;
@@ -641,7 +712,8 @@ cudaError_t launch_cell(StepArgs a, cudaStream_t s)
     if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
     if (REC && a.rec == nullptr) return cudaErrorInvalidValue;
     if (MU && a.inv_mu == nullptr) return cudaErrorInvalidValue;
-    step_kernel_cell<MODE, S, kBX, REC, MU><<<a.nblk_main, kBX, 0, s>>>(a);
+    if (ANA != (a.tfsf == 2)) return cudaErrorInvalidValue;
+    step_kernel_cell<MODE, S, kBX, REC, MU, ANA><<<a.nblk_main, kBX, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -722,6 +794,22 @@ cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_
     case 6: return launch_cell<2, float, false, true>(a, s);
     case 7: return launch_cell<2, __half, false, true>(a, s);
     case 8: return launch_cell<2, __nv_bfloat16, false, true>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step_analytic(int mode, int storage, const StepArgs &a, cudaStream_t s)
+{
+    switch (mode * 3 + storage) {
+    case 0: return launch_cell<0, float, false, true, true>(a, s);
+    case 1: return launch_cell<0, __half, false, true, true>(a, s);
+    case 2: return launch_cell<0, __nv_bfloat16, false, true, true>(a, s);
+    case 3: return launch_cell<1, float, false, true, true>(a, s);
+    case 4: return launch_cell<1, __half, false, true, true>(a, s);
+    case 5: return launch_cell<1, __nv_bfloat16, false, true, true>(a, s);
+    case 6: return launch_cell<2, float, false, true, true>(a, s);
+    case 7: return launch_cell<2, __half, false, true, true>(a, s);
+    case 8: return launch_cell<2, __nv_bfloat16, false, true, true>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

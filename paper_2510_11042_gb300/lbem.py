@@ -25,6 +25,8 @@ LBEM_ERR_TIMEOUT = -5
 LBEM_ERR_STATE = -6
 
 LBEM_D3Q7 = 0
+LBEM_SOURCE_LINE = 0
+LBEM_SOURCE_ANALYTIC = 1
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 MODE = {"ez": 0, "hz": 1, "3d": 2}
 
@@ -47,7 +49,8 @@ class PlaneWaveDesc(ctypes.Structure):
                 ("ramp_periods", ctypes.c_double),
                 ("tfsf_lo", ctypes.c_int32 * 3), ("tfsf_hi", ctypes.c_int32 * 3),
                 ("ntff_lo", ctypes.c_int32 * 3), ("ntff_hi", ctypes.c_int32 * 3),
-                ("center", ctypes.c_double * 3), ("source_index", ctypes.c_int32)]
+                ("center", ctypes.c_double * 3), ("source_index", ctypes.c_int32),
+                ("source_kind", ctypes.c_int32), ("origin", ctypes.c_double * 3)]
 
 
 class NtffDesc(ctypes.Structure):
@@ -164,6 +167,8 @@ def plane_wave_desc(wave) -> PlaneWaveDesc:
     d.ntff_hi[:] = wave.ntff_hi
     d.center[:] = wave.center
     d.source_index = wave.source_index
+    d.source_kind = LBEM_SOURCE_ANALYTIC if getattr(wave, "analytic", False) else LBEM_SOURCE_LINE
+    d.origin[:] = getattr(wave, "origin", (0.0, 0.0, 0.0))
     return d
 
 

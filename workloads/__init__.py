@@ -56,6 +56,8 @@ class PlaneWave:
     ntff_hi: Tuple[int, int, int] = (0, 0, 0)
     center: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     source_index: int = -1     # node of the 1D incident line that is driven
+    analytic: bool = False     # closed-form source instead of the line (any direction)
+    origin: Tuple[float, float, float] = (0.0, 0.0, 0.0)   # analytic: where tau = t
 
 
 @dataclass
@@ -232,6 +234,25 @@ def adjoint_problem(n=512, side=60.0, design=128, seed=7, wavelength=40.0, w=20,
     return replace(p, name=f"adjoint_hexagon_{mode}_{n}", eps=eps,
                    meta=dict(p.meta, design_lo=c0, design=design,
                              angles=(0.0, math.pi / 4, math.pi / 2)))
+
+
+def planar_problem(pol="s", n=200, x_interface=100, eps_in=2.25, wavelength=40.0, w=10,
+                   theta_deg=30.0, x_source=20, steps=1500) -> Problem:
+    """Planar interface (Sec. 3.1): eps_r = eps_in for x >= x_interface, a plane
+    wave at theta from +x in the xy plane (s: E along z, EZ mode; p: H along z,
+    HZ mode) from the closed-form source on the one-sided total-field region
+    x >= x_source, kept 5 cells clear of the absorbing layer in y."""
+    th = math.radians(theta_deg)
+    d = (math.cos(th), math.sin(th), 0.0)
+    p = (0.0, 0.0, 1.0) if pol == "s" else (-math.sin(th), math.cos(th), 0.0)
+    eps = halfspace_eps(n, n, x_interface, eps_in)
+    wave = PlaneWave(direction=d, polarization=p, wavelength=wavelength, amplitude=1.0,
+                     ramp_periods=3.0, tf_lo=(x_source, w + 5, 0), tf_hi=(10 ** 6, n - 1 - w - 5, 0),
+                     ntff_lo=(0, 0, 0), ntff_hi=(0, 0, 0), center=(0.0, 0.0, 0.0), analytic=True,
+                     origin=(float(x_source), 0.0, 0.0))
+    return Problem(name=f"planar_{pol}_{n}", mode="ez" if pol == "s" else "hz", shape=(n, n, 1),
+                   eps=eps, absorber_width=w, sigma_max=DEFAULT_SIGMA_MAX, wave=wave, steps=steps,
+                   dft_periods=1, meta=dict(theta=th, eps_in=eps_in, x_interface=x_interface))
 
 
 def batched_problems(count=32, seed=20251011, w=16):
