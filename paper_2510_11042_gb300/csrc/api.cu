@@ -917,6 +917,17 @@ int32_t lbem_get_time(lbem_handle h, int64_t *t_out)
     return LBEM_OK;
 }
 
+// Chunks of the far-field projection per angle: enough blocks for the face
+// cells (4096 per chunk) and for the face columns (256 per chunk).
+static int far_field_chunks(const FaceGeom &g)
+{
+    const long long cells = g.cell_start[g.nfaces];
+    long long cols = 0;
+    for (int f = 0; f < g.nfaces; ++f) cols += g.nv[f];
+    const long long c = std::max((cells + 4095) / 4096, (cols + 255) / 256);
+    return (int)std::max<long long>(1, std::min<long long>(kMaxChunks, c));
+}
+
 static void centre_nodes(lbem_ctx *h, int *i0, int *i1)
 {
     const double c = h->wave.center[h->inc_axis];
@@ -948,9 +959,7 @@ int32_t lbem_far_field(lbem_handle h, const double *theta, const double *phi, in
         a.pol[c] = h->wave.pol[c];
     }
     centre_nodes(h, &a.center_i0, &a.center_i1);
-    const long long cells = h->faces.cell_start[h->faces.nfaces];
-    int chunks = (int)((cells + 4095) / 4096);
-    a.chunks = std::max(1, std::min(kMaxChunks, chunks));
+    a.chunks = far_field_chunks(h->faces);
     double *d_theta = h->scratch;
     double *d_phi = d_theta + kAngleBatch;
     double *d_s2 = d_phi + kAngleBatch;
@@ -1348,8 +1357,7 @@ int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, cons
         fa.pol[c] = h->wave.pol[c];
     }
     centre_nodes(h, &fa.center_i0, &fa.center_i1);
-    const long long cells = h->faces.cell_start[h->faces.nfaces];
-    fa.chunks = std::max(1, std::min(kMaxChunks, (int)((cells + 4095) / 4096)));
+    fa.chunks = far_field_chunks(h->faces);
     double *d_theta = h->scratch;
     double *d_phi = d_theta + kAngleBatch;
     double *d_s2 = d_phi + kAngleBatch;

@@ -171,6 +171,126 @@ __global__ void __launch_bounds__(kFFThreads) far_field_partial(const FarFieldAr
     }
 }
 
+// Column form of stage 1 (phase tables in shared memory).  The phase of face
+// cell (iu, iv) factorises as t_u(iu) t_v(iv) t_w, and so does the
+// trapezoidal weight, so one thread takes one face column (fixed iv; the
+// threads of a warp read consecutive iv, coalesced) and sums the tangential
+// phasors down the column with t_u(iu) w(iu) alone; the column factor
+// t_v(iv) w(iv) t_w multiplies the four column sums once, and J = n x H,
+// M = -n x E are formed from them.  Per (cell, angle) this is four complex
+// multiply-adds.  Blocks stride over chunks of kFFThreads columns.
+template <int MODE>
+__global__ void __launch_bounds__(kFFThreads) far_field_columns(const FarFieldArgs a)
+{
+    extern __shared__ double tab[];  // [2 * (n0 + n1 + n2)] (re, im)
+    const int ang = blockIdx.y;
+    const double th = a.theta[ang];
+    double rh[3];
+    if (MODE == 2) {
+        const double ph = a.phi[ang];
+        rh[0] = sin(th) * cos(ph);
+        rh[1] = sin(th) * sin(ph);
+        rh[2] = cos(th);
+    } else {
+        rh[0] = cos(th);
+        rh[1] = sin(th);
+        rh[2] = 0.0;
+    }
+    const int n0 = a.g.hi[0] - a.g.lo[0] + 1, n1 = a.g.hi[1] - a.g.lo[1] + 1,
+              n2 = a.g.hi[2] - a.g.lo[2] + 1;
+    const int toff[3] = {0, n0, n0 + n1};
+    for (int e = threadIdx.x; e < n0 + n1 + n2; e += blockDim.x) {
+        const int ax = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+        const double pos = a.g.lo[ax] + (e - toff[ax]);
+        double sp, cp;
+        sincos(a.k * rh[ax] * (pos - a.center[ax]), &sp, &cp);
+        tab[2 * e] = cp;
+        tab[2 * e + 1] = sp;
+    }
+    __syncthreads();
+
+    int ncols = 0;
+    for (int f = 0; f < a.g.nfaces; ++f) ncols += a.g.nv[f];
+    double acc[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) acc[m] = 0.0;
+
+    for (int col = blockIdx.x * kFFThreads + threadIdx.x; col < ncols; col += a.chunks * kFFThreads) {
+        int f = 0, iv = col;
+        while (iv >= a.g.nv[f]) iv -= a.g.nv[f++];
+        const int nu = a.g.nu[f], nv = a.g.nv[f];
+        const int ax = a.g.axis[f];
+        const int ua = ax == 2 ? 1 : 2, va = ax == 0 ? 1 : 0;
+        const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+        const int sH1 = slot_H(MODE, b1), sH2 = slot_H(MODE, b2);
+        const int sE1 = slot_E(MODE, b1), sE2 = slot_E(MODE, b2);
+        const long long plane = (long long)nu * nv;
+        const double *base = a.dft + a.g.off[f] + iv;
+        const double *tu = tab + 2 * toff[ua];
+        // column sums of t_u w_u X for X = H_b1, H_b2, E_b1, E_b2 (re, im)
+        double sH1r = 0, sH1i = 0, sH2r = 0, sH2i = 0, sE1r = 0, sE1i = 0, sE2r = 0, sE2i = 0;
+        for (int iu = 0; iu < nu; ++iu) {
+            double pr = tu[2 * iu], pi = tu[2 * iu + 1];
+            if (nu > 1 && (iu == 0 || iu == nu - 1)) {
+                pr *= 0.5;
+                pi *= 0.5;
+            }
+            const double *c = base + (long long)iu * nv;
+            if (sH1 >= 0) {
+                const double xr = c[(2 * sH1) * plane], xi = c[(2 * sH1 + 1) * plane];
+                sH1r = fma(pr, xr, fma(-pi, xi, sH1r));
+                sH1i = fma(pr, xi, fma(pi, xr, sH1i));
+            }
+            if (sH2 >= 0) {
+                const double xr = c[(2 * sH2) * plane], xi = c[(2 * sH2 + 1) * plane];
+                sH2r = fma(pr, xr, fma(-pi, xi, sH2r));
+                sH2i = fma(pr, xi, fma(pi, xr, sH2i));
+            }
+            if (sE1 >= 0) {
+                const double xr = c[(2 * sE1) * plane], xi = c[(2 * sE1 + 1) * plane];
+                sE1r = fma(pr, xr, fma(-pi, xi, sE1r));
+                sE1i = fma(pr, xi, fma(pi, xr, sE1i));
+            }
+            if (sE2 >= 0) {
+                const double xr = c[(2 * sE2) * plane], xi = c[(2 * sE2 + 1) * plane];
+                sE2r = fma(pr, xr, fma(-pi, xi, sE2r));
+                sE2i = fma(pr, xi, fma(pi, xr, sE2i));
+            }
+        }
+        // column factor t_v(iv) w_v(iv) t_w and the outward normal's sign
+        const int iw = a.g.side[f] ? a.g.hi[ax] - a.g.lo[ax] : 0;
+        const double *tv = tab + 2 * (toff[va] + iv), *tw = tab + 2 * (toff[ax] + iw);
+        double wv = 1.0;
+        if (nv > 1 && (iv == 0 || iv == nv - 1)) wv = 0.5;
+        const double sgn = a.g.side[f] ? 1.0 : -1.0;
+        const double cr = wv * (tv[0] * tw[0] - tv[1] * tw[1]);
+        const double ci = wv * (tv[0] * tw[1] + tv[1] * tw[0]);
+        // J_b1 = -sgn H_b2, J_b2 = sgn H_b1, M_b1 = sgn E_b2, M_b2 = -sgn E_b1
+        auto add = [&](int m, double s, double xr, double xi) {
+            acc[m] += s * (cr * xr - ci * xi);
+            acc[m + 1] += s * (cr * xi + ci * xr);
+        };
+        add(2 * b1, -sgn, sH2r, sH2i);
+        add(2 * b2, sgn, sH1r, sH1i);
+        add(6 + 2 * b1, sgn, sE2r, sE2i);
+        add(6 + 2 * b2, -sgn, sE1r, sE1i);
+    }
+
+    __shared__ double red[kFFThreads / 32][12];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+        const double v = warp_sum(acc[m]);
+        if (lane == 0) red[wid][m] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        double s = 0.0;
+        for (int wi = 0; wi < kFFThreads / 32; ++wi) s += red[wi][threadIdx.x];
+        a.partial[((long long)ang * a.chunks + blockIdx.x) * 12 + threadIdx.x] = s;
+    }
+}
+
 // Stage 2: one thread per angle; fixed-order sum over chunks, then Eq. 5/6.
 __global__ void far_field_finalize(const FarFieldArgs a)
 {
@@ -415,12 +535,12 @@ inline int grid_for(long long n, int threads)
 #define LBEM_FF_TABLES(MODE)                                                                 \
     do {                                                                                     \
         if (smem > 48 * 1024) {                                                              \
-            cudaError_t e_ = cudaFuncSetAttribute(far_field_partial<MODE, true>,             \
+            cudaError_t e_ = cudaFuncSetAttribute(far_field_columns<MODE>,                   \
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                   kFFTableMax * 2 * (int)sizeof(double));    \
             if (e_ != cudaSuccess) return e_;                                                \
         }                                                                                    \
-        far_field_partial<MODE, true><<<g1, kFFThreads, smem, s>>>(a);                       \
+        far_field_columns<MODE><<<g1, kFFThreads, smem, s>>>(a);                             \
     } while (0)
 
 cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launches)
