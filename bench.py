@@ -271,6 +271,7 @@ def run_gpu(args, rank, world, local_rank):
 
     K, Wm = args.steps, args.warmup
     main = one_storage("f32", K, Wm, True)
+    probe_2d = None if (args.no_batch or world > 1) else run_probe_2d(dev)
     batched = None if (args.no_batch or world > 1) else run_batched(dev)
     adjoint = None if (args.no_adjoint or world > 1) else run_adjoint(dev)
     secondary = {}
@@ -331,6 +332,8 @@ def run_gpu(args, rank, world, local_rank):
                 "periods_run": main["periods"], "incident_amplitude": round(main["incident"], 6)},
         "storage_modes": storage_modes,
     }
+    if probe_2d:
+        line["bandwidth_probe_2d"] = probe_2d
     if batched:
         line["batched"] = batched
     if adjoint:
@@ -419,6 +422,37 @@ def _batch_vs_sequential(dev, probs):
             "sequential_mlups": round(work / t_seq / 1e6, 1),
             "speedup": round(t_seq / t_batch, 3),
             "autotuned": {"blocks_per_sm": bps, "rows_per_item": rpi}}
+
+
+# ------------------------------------------------------------------ 2D bandwidth probe
+def run_probe_2d(dev, n=4096, updates=60):
+    """Step-kernel bandwidth of the 2D EZ path on a grid well above L2
+    (4096^2 x 21 populations, 2.8 GB in FP32): a cylinder of the cylinder
+    workload's proportions, CUDA events around `updates` lattice updates."""
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    p = W.cylinder_problem(n=n, x=5.0, wavelength=40.0, eps_in=2.25, w=20, mode="ez", periods=1)
+    hbm, _ = peaks()
+    out = {"workload": f"cylinder {n}x{n} EZ, lambda 40, W 20", "cells": n * n}
+    for st in ("f32", "f16"):
+        s = lbem.Solver(p.shape, p.eps, "ez", st, p.absorber_width, p.sigma_max, device=dev)
+        s.inject(p.wave)
+        s.step(10)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(s.stream)
+        s.step(updates)
+        ev[1].record(s.stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / updates
+        bc = b_cell("ez", st)
+        gbs = bc * n * n / (ms / 1e3) / 1e9
+        out[st] = {"kernel_ms": round(ms, 4), "mlups": round(n * n / (ms / 1e3) / 1e6, 1),
+                   "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ adjoint workload

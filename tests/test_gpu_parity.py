@@ -213,3 +213,20 @@ def test_reinject_keeps_the_total_field():
     s.inject(p.wave)
     after = s.populations()
     np.testing.assert_allclose(after, before, rtol=0, atol=1e-6 * np.abs(before).max())
+
+
+def test_sphere_far_field_mirror_symmetry():
+    """3D mirror symmetry (k along +z, E along x): the sphere, the boxes and the
+    source are symmetric under y -> -y (fields even) and x -> -x (fields odd), so
+    |S(theta, phi)|^2 = |S(theta, -phi)|^2 = |S(theta, pi - phi)|^2."""
+    p = W.sphere_subproblem()
+    s = gpu_solver(p)
+    th = np.radians(np.arange(0.0, 181.0, 3.0))
+    out = {}
+    for phd in (20.0, -20.0, 160.0, 45.0, -45.0, 135.0, 70.0, -70.0, 110.0):
+        out[phd] = s.far_field(th, np.full(th.size, math.radians(phd)))
+    for phd in (20.0, 45.0, 70.0):
+        assert rel_l2(out[-phd], out[phd]) <= TOL
+        assert rel_l2(out[180.0 - phd], out[phd]) <= TOL
+    # and the phi dependence is real: the E-plane and H-plane patterns differ
+    assert rel_l2(out[20.0], out[70.0]) > 1e-2
