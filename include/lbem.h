@@ -202,6 +202,15 @@ int32_t lbem_far_field(lbem_handle h, const double *theta_host, const double *ph
 /* |E_I| as used by lbem_far_field. */
 int32_t lbem_incident_amplitude(lbem_handle h, double *out_host);
 
+/* Field probes: the Q total-field populations (the stored value plus, inside
+ * the total-field box, the incident part) of n listed cells, at the stored
+ * state's time.  xyz_host: n (x, y, z) triplets inside the grid; out_host:
+ * n * Q floats, out[k * Q + q] in the population-plane order above.
+ * n <= LBEM_PROBE_MAX, else LBEM_ERR_ARG; a cell outside the grid is
+ * LBEM_ERR_ARG.  Synchronous. */
+#define LBEM_PROBE_MAX 4096
+int32_t lbem_probe(lbem_handle h, const int32_t *xyz_host, int32_t n, float *out_host);
+
 /* Copy the populations out / in, float32 [Q][nz][ny][nx] (layout above). */
 int32_t lbem_get_populations(lbem_handle h, float *out, int32_t out_on_device);
 int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t in_on_device);

@@ -283,13 +283,28 @@ class Run:
     same absorbing layer along that axis, and is driven at wave.source_index.
     """
 
-    def __init__(self, problem, record_dft=True):
+    def __init__(self, problem, record_dft=True, region=None):
+        """region = (lo, hi), inclusive global cell bounds: the main lattice then
+        covers only that box (global coordinates for the layer, the TF box and
+        the source; its own faces are clamped, so after k steps cells more than
+        k cells inside it are exact).  The incident line always spans the grid."""
         self.problem = problem
         self.t = 0  # steps done; state holds f*(t)
         w = problem.wave
         nx, ny, nz = problem.shape
-        self.main = Lattice(problem.shape, problem.eps, mu=getattr(problem, "mu", None),
-                            sponge_w=problem.absorber_width, sigma_max=problem.sigma_max)
+        mu = getattr(problem, "mu", None)
+        if region is None:
+            self.main = Lattice(problem.shape, problem.eps, mu=mu,
+                                sponge_w=problem.absorber_width, sigma_max=problem.sigma_max)
+        else:
+            lo, hi = [tuple(int(v) for v in b) for b in region]
+            sl = (slice(lo[2], hi[2] + 1), slice(lo[1], hi[1] + 1), slice(lo[0], hi[0] + 1))
+            shape = tuple(hi[a] - lo[a] + 1 for a in range(3))
+            self.main = Lattice(shape, np.asarray(problem.eps)[sl],
+                                mu=None if mu is None else np.asarray(mu)[sl], origin=lo,
+                                global_shape=problem.shape, sponge_w=problem.absorber_width,
+                                sigma_max=problem.sigma_max)
+            record_dft = False
         self.T = int(round(3 * w.wavelength))
         if abs(3 * w.wavelength - self.T) > 1e-9:
             raise ValueError("3*wavelength must be an integer (the period in steps)")

@@ -1049,6 +1049,29 @@ int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t on_device)
     return LBEM_OK;
 }
 
+int32_t lbem_probe(lbem_handle h, const int32_t *xyz, int32_t n, float *out)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (n < 0 || n > LBEM_PROBE_MAX || (n > 0 && (!xyz || !out)))
+        return fail(h, LBEM_ERR_ARG, "need 0..%d cells with xyz and out", LBEM_PROBE_MAX);
+    if (n == 0) return LBEM_OK;
+    for (int k = 0; k < n; ++k)
+        if (xyz[3 * k] < 0 || xyz[3 * k] >= h->g.nx || xyz[3 * k + 1] < 0 || xyz[3 * k + 1] >= h->g.ny ||
+            xyz[3 * k + 2] < 0 || xyz[3 * k + 2] >= h->g.nz)
+            return fail(h, LBEM_ERR_ARG, "probe cell %d (%d, %d, %d) is outside the grid", k, xyz[3 * k],
+                        xyz[3 * k + 1], xyz[3 * k + 2]);
+    // scratch: the cell list, then n * Q floats
+    int *d_xyz = (int *)h->scratch;
+    float *d_out = (float *)(h->scratch) + 3 * LBEM_PROBE_MAX;
+    CK(h, cudaMemcpyAsync(d_xyz, xyz, (size_t)n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_probe(h->g.mode, h->g.storage, h->f[h->cur], h->scale, h->P, h->g.ny, h->nxp, d_xyz, n,
+                       inc_view(h), d_out, h->stream));
+    h->launches += 1;
+    CK(h, cudaMemcpyAsync(out, d_out, (size_t)n * h->Q * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_status(h);
+}
+
 int32_t lbem_fields(lbem_handle h, float *E, float *H, int32_t on_device)
 {
     if (!h || !E || !H) return fail(h, LBEM_ERR_ARG, "NULL argument");

@@ -316,6 +316,8 @@ cudaError_t launch_unpack(int mode, int storage, void *f, long long P, int q, fl
 cudaError_t launch_add_incident(int mode, int storage, void *f, long long P, int Q, float scale,
                                 int nx, int ny, int nz, int nxp, const IncView &inc, float sign,
                                 cudaStream_t s);
+cudaError_t launch_probe(int mode, int storage, const void *f, float scale, long long P, int ny, int nxp,
+                         const int *xyz, int n, const IncView &inc, float *out, cudaStream_t s);
 cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv_eps, const float *inv_mu,
                           float scale, long long P, int nx, int ny, int nz, int nxp,
                           const IncView &inc, int comp, float *out, cudaStream_t s);

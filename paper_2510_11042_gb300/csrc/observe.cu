@@ -447,6 +447,30 @@ __global__ void add_incident_kernel(int mode, S *f, long long P, int Q, float sc
     }
 }
 
+// Total-field populations of n listed cells (x, y, z triplets): out[k][q].
+template <int MODE, class S>
+__global__ void probe_kernel(const S *f, float sc, long long P, int ny, int nxp, const int *xyz, int n,
+                             IncView inc, float *out)
+{
+    constexpr int Q = Planes<MODE>::Q;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n * Q; j += gridDim.x * blockDim.x) {
+        const int k = j / Q, q = j % Q;
+        const int x = xyz[3 * k], y = xyz[3 * k + 1], z = xyz[3 * k + 2];
+        const long long c = ((long long)z * ny + y) * nxp + x;
+        out[j] = ldv<S>(f + pop_index(MODE, (int)sizeof(S), P, q, c)) * sc + inc_at(inc, q, x, y, z);
+    }
+}
+
+template <int MODE, class S>
+static cudaError_t probe_t(const void *f, float sc, long long P, int ny, int nxp, const int *xyz, int n,
+                           const IncView &inc, float *out, cudaStream_t s)
+{
+    const int total = n * Planes<MODE>::Q;
+    probe_kernel<MODE, S><<<(total + 255) / 256, 256, 0, s>>>((const S *)f, sc, P, ny, nxp, xyz, n, inc,
+                                                              out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ fields & energy
 template <int MODE, class S>
 __device__ __forceinline__ void cell_DB(const S *f, float sc, long long P, long long c,
@@ -693,6 +717,12 @@ cudaError_t launch_fields(int mode, int storage, const void *f, const float *inv
                           const IncView &inc, int comp, float *out, cudaStream_t s)
 {
     LBEM_DISPATCH(fields_t, f, inv_eps, inv_mu, scale, P, nx, ny, nz, nxp, inc, comp, out, s)
+}
+
+cudaError_t launch_probe(int mode, int storage, const void *f, float scale, long long P, int ny, int nxp,
+                         const int *xyz, int n, const IncView &inc, float *out, cudaStream_t s)
+{
+    LBEM_DISPATCH(probe_t, f, scale, P, ny, nxp, xyz, n, inc, out, s)
 }
 
 cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv_eps, const float *inv_mu,

@@ -101,6 +101,7 @@ _SIGS = {
     "lbem_forward_checkpointed": (_I32, [_P, _I64, _I32, _P, ctypes.c_size_t]),
     "lbem_adjoint": (_I32, [_P, _P, _P, _P, _I32, _P, _I32, ctypes.POINTER(ctypes.c_double)]),
     "lbem_adjoint_timing": (_I32, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "lbem_probe": (_I32, [_P, _P, _I32, _P]),
     "lbem_sync": (_I32, [_P]),
     "lbem_destroy": (None, [_P]),
     "lbem_last_error": (ctypes.c_char_p, [_P]),
@@ -426,6 +427,17 @@ def lbem_adjoint_timing(h):
     return r.value, b.value
 
 
+LBEM_PROBE_MAX = 4096
+
+
+def lbem_probe(h, xyz, q):
+    """Total-field populations [n][q] of the cells xyz ([n][3] ints: x, y, z)."""
+    xyz = np.ascontiguousarray(xyz, np.int32).reshape(-1, 3)
+    out = np.empty((xyz.shape[0], q), np.float32)
+    _check(lib().lbem_probe(h, xyz.ctypes.data, xyz.shape[0], out.ctypes.data), h)
+    return out
+
+
 def lbem_sync(h):
     _check(lib().lbem_sync(h), h)
 
@@ -539,6 +551,10 @@ class Solver:
 
     def sync(self):
         lbem_sync(self.h)
+
+    def probe(self, xyz):
+        """Total-field populations [n][Q] of the cells xyz ([n][3]: x, y, z)."""
+        return lbem_probe(self.h, xyz, self.Q)
 
     def forward_checkpointed(self, n_steps, K):
         """Take n_steps steps from t = 0 keeping every K-th state for lbem_adjoint."""

@@ -202,3 +202,45 @@ def test_error_metrics_of_eqs_12_13_closed_forms():
     s = ref.copy()
     s[2] += 0.8
     assert metrics.normalized_rms(s, ref) == pytest.approx(0.8 / 2.0 / 4.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("analytic", [False, True])
+def test_subbox_run_matches_full_run_inside_the_light_cone(analytic):
+    """A run restricted to a box of the grid (global coordinates for the layer,
+    the TF box and the source; clamped at its own faces) reproduces the full
+    run exactly at cells more than k cells inside the box after k steps, and
+    everywhere the box touches the real grid boundary."""
+    import dataclasses
+    import math
+    import workloads as W
+    shape = (24, 20, 28)
+    nx, ny, nz = shape
+    eps = W.random_eps(shape, 1.0, 4.0, 3).astype(np.float64)
+    wave = W.axis_wave("3d", shape, 4, 4.0, gap_ntff=1, gap_tf=2)
+    if analytic:
+        th = math.radians(35.0)
+        wave = dataclasses.replace(wave, direction=(math.sin(th), 0.0, math.cos(th)),
+                                   polarization=(math.cos(th), 0.0, -math.sin(th)), analytic=True,
+                                   origin=(3.0, 2.0, 1.0), ramp_periods=0.0)
+    p = W.Problem("sub", "3d", shape, eps, 4, 0.3, wave, 40, 1)
+    rng = np.random.default_rng(9)
+    f0 = rng.standard_normal((nz, ny, nx, lb.NQ))
+    k = 4
+    full = lb.Run(p, record_dft=False)
+    full.main.f = f0.reshape(-1, lb.NQ).copy()
+    full.step(k)
+    ff = full.main.f.reshape(nz, ny, nx, lb.NQ)
+    for c in [(0, 0, 0), (23, 19, 27), (5, 6, 7), (12, 10, 14), (4, 17, 26), (20, 3, 9)]:
+        lo = [max(0, c[a] - (k + 1)) for a in range(3)]
+        hi = [min(shape[a] - 1, c[a] + (k + 1)) for a in range(3)]
+        sub = lb.Run(p, region=(lo, hi))
+        sub.main.f = f0[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1].reshape(-1, lb.NQ).copy()
+        sub.step(k)
+        sn = [hi[a] - lo[a] + 1 for a in range(3)]
+        fs = sub.main.f.reshape(sn[2], sn[1], sn[0], lb.NQ)
+        got = fs[c[2] - lo[2], c[1] - lo[1], c[0] - lo[0]]
+        assert np.max(np.abs(got - ff[c[2], c[1], c[0]])) < 1e-12
+        # a cell near the box face (inside the grid) is not exact: the check has teeth
+        if lo[0] > 0:
+            edge = fs[c[2] - lo[2], c[1] - lo[1], 0]
+            assert np.max(np.abs(edge - ff[c[2], c[1], lo[0]])) > 1e-6

@@ -134,6 +134,14 @@ def random_eps(shape, lo: float, hi: float, seed: int) -> np.ndarray:
     return rng.uniform(lo, hi, size=(nz, ny, nx)).astype(np.float32)
 
 
+def random_state_f32(mode: str, shape, seed: int) -> np.ndarray:
+    """Seeded N(0,1) populations drawn directly in float32 (for grids where a
+    float64 draw would not fit in host memory), [Q][nz][ny][nx]."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n_planes(mode), nz, ny, nx), dtype=np.float32)
+
+
 def random_state(mode: str, shape, seed: int) -> np.ndarray:
     """Seeded N(0,1) populations in the library's plane order, [Q][nz][ny][nx]."""
     nx, ny, nz = shape
