@@ -201,3 +201,51 @@ def test_empty_calls():
     with pytest.raises(lbem.LbemError):
         s.probe(np.zeros((lbem.LBEM_PROBE_MAX + 1, 3), np.int32))
     s.close()
+
+
+@pytest.mark.parametrize("mode,col", [("ez", 1), ("hz", 2)])
+def test_cylinder_workload_matches_mie_and_symmetry(mode, col):
+    """The full 1024^2 cylinder workload (x = 5, eps_r = 2.25, lambda = 40,
+    W = 20, 40 periods = 4800 steps): |S|^2 against the Lorenz-Mie series
+    (TM = EZ, TE = HZ; Eq. 13 at the level the paper reports, <= 5e-3) and the
+    mirror symmetry |S(theta)|^2 = |S(-theta)|^2."""
+    from paper_2510_11042_gb300 import lbem
+    _free_cache()
+    p = W.cylinder_problem(mode=mode)
+    s = lbem.Solver(p.shape, p.eps, mode, "f32", p.absorber_width, p.sigma_max)
+    s.inject(p.wave)
+    s.set_dft_window(p.dft_start, p.dft_periods)
+    s.step(p.steps)
+    th = np.radians(np.arange(181.0))
+    s2 = s.far_field(th)
+    ref = np.loadtxt(os.path.join(GOLDEN, "mie_cylinder_x5_m1.5.txt"))[:, col]
+    nrms = np.sqrt(np.mean((s2 - ref) ** 2)) / np.max(ref)
+    print(f"[cylinder 1024^2 {mode}] Mie normalized RMS {nrms:.2e}")
+    assert nrms <= 5e-3
+    mirror = s.far_field(-th)
+    assert np.linalg.norm(mirror - s2) <= 1e-5 * np.linalg.norm(s2)
+    s.close()
+
+
+def test_cylinder_workload_sampled_parity():
+    """The 1024^2 cylinder workload from a seeded random state, 4 steps: sampled
+    cells against the oracle's light-cone runs (FP32 bar 1e-5)."""
+    from paper_2510_11042_gb300 import lbem
+    _free_cache()
+    p = W.cylinder_problem(mode="ez")
+    init = W.random_state_f32("ez", p.shape, 77)
+    s = lbem.Solver(p.shape, p.eps, "ez", "f32", p.absorber_width, p.sigma_max)
+    s.set_populations(init)
+    s.inject(p.wave)
+    k = 4
+    s.step(k)
+    n = p.shape[0]
+    rng = np.random.default_rng(8)
+    cells = [(0, 0, 0), (n - 1, n - 1, 0), (p.wave.tf_lo[0], n // 2, 0), (n // 2, p.wave.ntff_hi[1], 0),
+             (n // 2 + 31, n // 2, 0), (3, n - 7, 0)] + \
+            [(int(rng.integers(n)), int(rng.integers(n)), 0) for _ in range(10)]
+    got = s.probe(cells)
+    s.close()
+    exp = _oracle_cells(p, cells, k, init_planes=init)
+    err = np.linalg.norm(got - exp, axis=1) / np.linalg.norm(exp, axis=1)
+    assert err.max() <= 1e-5, err

@@ -4,6 +4,7 @@ Bar: relative L2 <= 1e-5 for FP32 storage on populations, DFT phasors and the
 far-field intensity, against the FP64 oracle on the same seeded inputs.
 FP16/BF16 storage errors are reported and checked against looser bounds.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -230,3 +231,30 @@ def test_sphere_far_field_mirror_symmetry():
         assert rel_l2(out[180.0 - phd], out[phd]) <= TOL
     # and the phi dependence is real: the E-plane and H-plane patterns differ
     assert rel_l2(out[20.0], out[70.0]) > 1e-2
+
+
+def test_high_contrast_parity_and_stability():
+    """High permittivity contrast (eps_r up to 20, as in the paper's cylinder
+    sweeps): FP32 parity with the oracle from a random state, and a long run of
+    an eps_r = 20 cylinder whose field energy stays bounded."""
+    from oracle import lb
+    p = random_problem("ez", (96, 80, 1))
+    eps = W.random_eps(p.shape, 1.0, 20.0, 4242)
+    eps[p.eps == 1.0] = 1.0                  # vacuum on the box surfaces, as in random_problem
+    p = dataclasses.replace(p, eps=eps, steps=400)
+    init = W.random_state("ez", p.shape, 4243)
+    s = gpu_solver(p, init=init, steps=0)
+    r = lb.Run(p)
+    r.main.f = planes_to_oracle(init.astype(np.float64), "ez")
+    s.step(p.steps)
+    r.step(p.steps)
+    assert rel_l2(s.populations(), oracle_to_planes(r.main.f, "ez", p.shape)) <= TOL
+    c = W.cylinder_problem(n=192, x=3.0, wavelength=24.0, eps_in=20.0, w=16, mode="ez", periods=60,
+                           gap_ntff=2, gap_tf=2)
+    sc = gpu_solver(c, steps=0)
+    energies = []
+    for _ in range(6):
+        sc.step(c.steps // 6)
+        energies.append(sc.energy())
+    assert all(np.isfinite(energies))
+    assert max(energies[3:]) <= 2.0 * max(energies[:3])   # steady state, no growth
