@@ -401,7 +401,7 @@ def _batch_vs_sequential(dev, probs):
     batch.run([p.steps for p in probs], autotune=True)
     torch.cuda.synchronize(dev)
     t_batch = time.perf_counter() - t0
-    bps, rpi, _ = batch.config()
+    bps, rpi, _, split = batch.config()
     batch.close()
     for s in sol:
         s.close()
@@ -421,7 +421,7 @@ def _batch_vs_sequential(dev, probs):
     return {"cell_updates": work, "persistent_mlups": round(work / t_batch / 1e6, 1),
             "sequential_mlups": round(work / t_seq / 1e6, 1),
             "speedup": round(t_seq / t_batch, 3),
-            "autotuned": {"blocks_per_sm": bps, "rows_per_item": rpi}}
+            "autotuned": {"blocks_per_sm": bps, "rows_per_item": rpi, "split": split}}
 
 
 # ------------------------------------------------------------------ 2D bandwidth probe

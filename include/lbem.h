@@ -254,17 +254,25 @@ int32_t lbem_get_storage_scale(lbem_handle h, float *scale_out);
  * (problems that are done drop out); with autotune the first call times a
  * few candidate launch shapes (blocks per SM, rows per work item) on its
  * first steps, which count as real steps (the results do not depend on the
- * shape), and keeps the fastest.  The handles' own streams are synchronised
- * first; the batch runs on cuda_stream and returns when it is done.
- * LBEM_ERR_TIMEOUT reports a grid-barrier wait that ran out.  workspace: as
- * in lbem_create (NULL: the library allocates it). */
+ * shape), and keeps the fastest.  It then also times split schedules, in
+ * which grids of at least 2^k cells (k = 16..20) advance by one plain step
+ * launch each (such a grid fills much of the GPU by itself, and the
+ * persistent kernel's grid barrier would only add to its step) while the rest
+ * share the persistent launch, and keeps one when it is faster
+ * (lbem_batch_config's split = 1).  autotune = 0 runs everything persistent
+ * at the largest resident shape; autotune = 2 forces the split schedule at
+ * 2^19 cells without timing.
+ * The handles' own streams are synchronised first; the batch runs on
+ * cuda_stream and returns when it is done.  LBEM_ERR_TIMEOUT reports a
+ * grid-barrier wait that ran out.  workspace: as in lbem_create (NULL: the
+ * library allocates it). */
 typedef struct lbem_batch_ctx *lbem_batch;
 int32_t lbem_batch_workspace_bytes(int32_t count, size_t *bytes_out);
 int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, void *cuda_stream,
                           void *workspace, size_t workspace_bytes, lbem_batch *out);
 int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t autotune);
 int32_t lbem_batch_config(lbem_batch b, int32_t *blocks_per_sm, int32_t *rows_per_item,
-                          double *ms_per_step);
+                          double *ms_per_step, int32_t *split);
 int64_t lbem_batch_launches(lbem_batch b);
 const char *lbem_batch_last_error(lbem_batch b);
 void lbem_batch_destroy(lbem_batch b);

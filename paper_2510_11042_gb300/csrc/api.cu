@@ -666,16 +666,10 @@ struct lbem_batch_ctx {
     int *status = nullptr;           // device
     int mode = 0, storage = 0;
     int tuned = 0, best_bps = 0, best_rpi = 1;
+    int split = 0;                   // large grids stepped by plain launches, the rest persistent
+    long long split_cells = 0;       // size from which a grid counts as large
     double best_ms = 0.0;
     int64_t launches = 0;
-    // adjoint: checkpoints of lbem_forward_checkpointed and the backward buffers
-    char *adj_ws = nullptr;
-    size_t adj_bytes = 0;
-    bool adj_owns = false;
-    bool adj_valid = false;
-    int64_t adj_steps = 0;
-    int adj_K = 0;
-    double adj_replay_ms = 0.0, adj_backward_ms = 0.0;  // of the last lbem_adjoint
     char err[512];
 };
 
@@ -749,16 +743,19 @@ extern "C" int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, 
 }
 
 // Run every problem of the batch min(left_i, chunk) steps in one cooperative launch.
+// Advance the problems listed in group by min(left, chunk) steps in one
+// persistent launch.
 static int batch_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t chunk, int bps, int rpi,
-                       cudaEvent_t ev0, cudaEvent_t ev1)
+                       cudaEvent_t ev0, cudaEvent_t ev1, const std::vector<int> &group)
 {
-    const int n = (int)b->hs.size();
+    const int n = (int)group.size();
     std::vector<BatchProblem> tab(n);
     int items = 0;
     int64_t max_steps = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int gi = 0; gi < n; ++gi) {
+        const int i = group[gi];
         lbem_ctx *h = b->hs[i];
-        BatchProblem &P = tab[i];
+        BatchProblem &P = tab[gi];
         std::memset(&P, 0, sizeof P);
         fill_common_args(h, P.a);
         P.a.nblk_x = (h->g.nx + 127) / 128;
@@ -816,9 +813,10 @@ static int batch_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t ch
     if (ev1) cudaEventRecord(ev1, b->stream);
     if (e != cudaSuccess) return bfail(b, LBEM_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     b->launches += 1;
-    for (int i = 0; i < n; ++i) {
+    for (int gi = 0; gi < n; ++gi) {
+        const int i = group[gi];
         lbem_ctx *h = b->hs[i];
-        const int64_t k = tab[i].steps;
+        const int64_t k = tab[gi].steps;
         h->t += k;
         h->cur ^= (int)(k & 1);
         left[i] -= k;
@@ -828,6 +826,40 @@ static int batch_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t ch
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return bfail(b, LBEM_ERR_CUDA, "batch run: %s", cudaGetErrorString(cudaGetLastError()));
     if (st & 2) return bfail(b, LBEM_ERR_TIMEOUT, "a grid-barrier wait of the batched kernel ran out");
+    return LBEM_OK;
+}
+
+// Grids of at least this many cells fill the GPU with one plain launch per
+// step; the persistent kernel's grid barrier and shared-memory arguments only
+// pay off below it.
+constexpr long long kSplitCells = 1LL << 19;
+
+// The large grids advance by plain step launches on the batch stream, the
+// others in one persistent launch; ev0 / ev1 (optional) bracket both.
+static int split_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t chunk, int bps, int rpi,
+                       const std::vector<int> &small, const std::vector<int> &big, cudaEvent_t ev0,
+                       cudaEvent_t ev1)
+{
+    if (ev0) cudaEventRecord(ev0, b->stream);
+    for (int i : big) {
+        lbem_ctx *h = b->hs[i];
+        const int64_t k = std::min<int64_t>(left[i], chunk);
+        cudaStream_t own = h->stream;
+        h->stream = b->stream;
+        const int64_t l0 = h->launches;
+        const int rc = lbem_step(h, k);
+        h->stream = own;
+        if (rc != LBEM_OK) return bfail(b, rc, "step of problem %d: %s", i, h->err);
+        b->launches += h->launches - l0;
+        left[i] -= k;
+    }
+    if (!small.empty()) {
+        const int rc = batch_chunk(b, left, chunk, bps, rpi, nullptr, nullptr, small);
+        if (rc != LBEM_OK) return rc;
+    }
+    if (ev1) cudaEventRecord(ev1, b->stream);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return bfail(b, LBEM_ERR_CUDA, "batch run: %s", cudaGetErrorString(cudaGetLastError()));
     return LBEM_OK;
 }
 
@@ -843,7 +875,14 @@ extern "C" int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t au
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bfail(b, LBEM_ERR_CUDA, "handle stream failed");
     const int max_bps = batch_max_blocks_per_sm(b->mode, b->storage);
     if (max_bps < 1) return bfail(b, LBEM_ERR_CUDA, "the batched kernel cannot be resident");
-    if (autotune && !b->tuned) {
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    auto partition = [&](long long cells, std::vector<int> &small, std::vector<int> &big) {
+        small.clear();
+        big.clear();
+        for (int i = 0; i < n; ++i) (b->hs[i]->ncell >= cells ? big : small).push_back(i);
+    };
+    if (autotune == 1 && !b->tuned) {
         // time a few steps of each candidate; steps taken while tuning count
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -858,7 +897,7 @@ extern "C" int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t au
                 int64_t active = 0;
                 for (int64_t v : left) active = std::max(active, std::min<int64_t>(v, trial));
                 if (active < trial) break;
-                int rc = batch_chunk(b, left, trial, bps, rpi_c[ir], e0, e1);
+                int rc = batch_chunk(b, left, trial, bps, rpi_c[ir], e0, e1, all);
                 if (rc != LBEM_OK) {
                     cudaEventDestroy(e0);
                     cudaEventDestroy(e1);
@@ -873,6 +912,29 @@ extern "C" int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t au
                 }
             }
         }
+        // split schedules (plain launches for the grids of at least 2^k cells)
+        // against the all-persistent one, over the same number of trial steps
+        for (int lg = 20; lg >= 16 && b->best_bps > 0; --lg) {
+            std::vector<int> small, big;
+            partition(1LL << lg, small, big);
+            if (big.empty()) continue;
+            int64_t active = 0;
+            for (int64_t v : left) active = std::max(active, std::min<int64_t>(v, trial));
+            if (active < trial) break;
+            int rc = split_chunk(b, left, trial, b->best_bps, b->best_rpi, small, big, e0, e1);
+            if (rc != LBEM_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return rc;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / trial < best) {
+                best = ms / trial;
+                b->split = 1;
+                b->split_cells = 1LL << lg;
+            }
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (b->best_bps > 0) {
@@ -880,16 +942,28 @@ extern "C" int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t au
             b->best_ms = best;
         }
     }
+    if (autotune == 2) {
+        b->split = 1;
+        b->split_cells = kSplitCells;
+    }
     const int bps = b->best_bps > 0 ? b->best_bps : max_bps;
+    std::vector<int> small, big;
+    if (b->split) partition(b->split_cells, small, big);
+    if (b->split && !big.empty()) {
+        int64_t remaining = 0;
+        for (int64_t v : left) remaining = std::max(remaining, v);
+        return split_chunk(b, left, remaining, bps, b->best_rpi, small, big, nullptr, nullptr);
+    }
     int64_t remaining = 0;
     for (int64_t v : left) remaining = std::max(remaining, v);
-    return batch_chunk(b, left, remaining, bps, b->best_rpi, nullptr, nullptr);
+    return batch_chunk(b, left, remaining, bps, b->best_rpi, nullptr, nullptr, all);
 }
 
 extern "C" int32_t lbem_batch_config(lbem_batch b, int32_t *blocks_per_sm, int32_t *rows_per_item,
-                                     double *ms_per_step)
+                                     double *ms_per_step, int32_t *split)
 {
     if (!b) return bfail(nullptr, LBEM_ERR_ARG, "NULL batch");
+    if (split) *split = b->split;
     if (blocks_per_sm) *blocks_per_sm = b->best_bps;
     if (rows_per_item) *rows_per_item = b->best_rpi;
     if (ms_per_step) *ms_per_step = b->best_ms;

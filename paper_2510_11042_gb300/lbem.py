@@ -93,7 +93,7 @@ _SIGS = {
     "lbem_batch_create": (_I32, [ctypes.POINTER(_P), _I32, _P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "lbem_batch_run": (_I32, [_P, ctypes.POINTER(_I64), _I32]),
     "lbem_batch_config": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
-                                 ctypes.POINTER(ctypes.c_double)]),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I32)]),
     "lbem_batch_launches": (_I64, [_P]),
     "lbem_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbem_batch_destroy": (None, [_P]),
@@ -338,14 +338,19 @@ def lbem_batch_create(handles, stream=None, workspace=None) -> int:
 
 
 def lbem_batch_run(b, steps, autotune=True):
+    """autotune: True (timed choice of shape and schedule), False (persistent,
+    largest resident shape) or "split" (split schedule without timing)."""
     arr = (_I64 * len(steps))(*[int(v) for v in steps])
-    _bcheck(lib().lbem_batch_run(b, arr, 1 if autotune else 0), b)
+    mode = 2 if autotune == "split" else (1 if autotune else 0)
+    _bcheck(lib().lbem_batch_run(b, arr, mode), b)
 
 
 def lbem_batch_config(b):
-    bps, rpi, ms = _I32(), _I32(), ctypes.c_double()
-    _bcheck(lib().lbem_batch_config(b, ctypes.byref(bps), ctypes.byref(rpi), ctypes.byref(ms)), b)
-    return bps.value, rpi.value, ms.value
+    """(blocks per SM, rows per work item, ms per trial step, split schedule)."""
+    bps, rpi, ms, split = _I32(), _I32(), ctypes.c_double(), _I32()
+    _bcheck(lib().lbem_batch_config(b, ctypes.byref(bps), ctypes.byref(rpi), ctypes.byref(ms),
+                                    ctypes.byref(split)), b)
+    return bps.value, rpi.value, ms.value, bool(split.value)
 
 
 def lbem_batch_launches(b) -> int:

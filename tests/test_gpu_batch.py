@@ -30,7 +30,7 @@ def test_batch_matches_single_runs():
     batched = [gpu_solver(p, steps=0) for p in probs]
     batch = lbem.Batch(batched)
     batch.run([p.steps for p in probs], autotune=True)
-    bps, rpi, ms = batch.config()
+    bps, rpi, ms, split = batch.config()
     assert bps >= 1 and rpi in (1, 2, 4) and ms > 0
     th, _ = angles("ez")
     for p, s1, s2 in zip(probs, singles, batched):
@@ -53,4 +53,24 @@ def test_batch_partial_steps_then_single_steps():
     for a, b in zip(sol, ref):
         assert a.time == b.time == 101
         assert rel_l2(a.populations(), b.populations()) <= 1e-6
+    batch.close()
+
+
+@pytest.mark.parametrize("schedule", ["split", True])
+def test_batch_with_large_grid(schedule):
+    """A batch mixing a grid of >= 2^19 cells (stepped by plain launches under
+    the split schedule) with small ones matches single runs either way."""
+    from paper_2510_11042_gb300 import lbem
+    probs = [W.with_steps(W.cylinder_problem(n=768, x=4.0, wavelength=16.0, eps_in=2.25, w=16, mode="ez",
+                                             periods=1), 150)] + problems()
+    singles = [gpu_solver(p) for p in probs]
+    batched = [gpu_solver(p, steps=0) for p in probs]
+    batch = lbem.Batch(batched)
+    batch.run([p.steps for p in probs], autotune=schedule)
+    split = batch.config()[3]
+    if schedule == "split":
+        assert split
+    for p, s1, s2 in zip(probs, singles, batched):
+        assert s2.time == p.steps
+        assert rel_l2(s2.populations(), s1.populations()) <= 1e-6
     batch.close()
