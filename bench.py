@@ -490,6 +490,7 @@ def run_adjoint(dev, K=200):
     launches = s.kernel_launches() - l0
     s.close()
     torch.cuda.empty_cache()
+    probe = _adjoint_probe_3d(dev)
     hbm, _ = peaks()
     q, ne = 21, 1
     bytes_adj = 2 * q * 4 + 4 + 4 * ne + 16
@@ -510,7 +511,36 @@ def run_adjoint(dev, K=200):
             "adjoint_step_roofline": {"bound": "hbm", "bytes_per_cell": bytes_adj,
                                       "achieved": round(ach, 1), "peak": hbm,
                                       "unit": "GB/s", "frac": round(ach / hbm, 4),
-                                      "note": "working set L2-resident at 512^2"}}
+                                      "note": "working set L2-resident at 512^2"},
+            "hbm_probe_3d": probe}
+
+
+def _adjoint_probe_3d(dev, n=128, K=60):
+    """The adjoint kernels on a 3D grid well above L2 (128^3 sphere, lambda 8,
+    240 steps; adjoint populations 0.7 GB): replay and backward bandwidth."""
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    p = W.sphere_problem(n=n, x=3.0, wavelength=8.0, eps_in=2.25, w=10, periods=10, gap_ntff=2, gap_tf=2)
+    cells = n ** 3
+    s = lbem.Solver(p.shape, p.eps, "3d", "f32", p.absorber_width, p.sigma_max, device=dev)
+    s.inject(p.wave)
+    s.set_dft_window(p.dft_start, p.dft_periods)
+    s.forward_checkpointed(p.steps, K)
+    s.adjoint([0.0], [0.0], [1.0])          # warm
+    s.adjoint([0.0], [0.0], [1.0])
+    replay_ms, back_ms = lbem.lbem_adjoint_timing(s.h)
+    s.close()
+    torch.cuda.empty_cache()
+    hbm, _ = peaks()
+    b_back = 2 * 42 * 4 + 4 + 12 + 16
+    b_rep = b_cell("3d", "f32") + 12
+    gb = b_back * cells * p.steps / (back_ms / 1e3) / 1e9
+    gr = b_rep * cells * p.steps / (replay_ms / 1e3) / 1e9
+    return {"workload": f"sphere {n}^3, lambda 8, {p.steps} steps, checkpoint every {K}, FP32",
+            "backward": {"ms_per_step": round(back_ms / p.steps, 4), "bytes_per_cell": b_back,
+                         "achieved_gbs": round(gb, 1), "hbm_frac": round(gb / hbm, 4)},
+            "replay": {"ms_per_step": round(replay_ms / p.steps, 4), "bytes_per_cell": b_rep,
+                       "achieved_gbs": round(gr, 1), "hbm_frac": round(gr / hbm, 4)}}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -560,10 +590,24 @@ def cpu_baseline(size, budget_s=15.0):
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return {"value": round(slab.cells * n / el / 1e6, 3), "unit": "MLUPS", "cores": cpu_cores(),
-            "kind": "oracle",
+    value = slab.cells * n / el / 1e6
+    # the same sample on one core
+    from oracle import lb
+    lb.set_threads(1)
+    t0 = time.perf_counter()
+    n1 = 0
+    while True:
+        slab.step(1)
+        n1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 >= budget_s / 3:
+            break
+    lb.set_threads(cpu_cores())
+    return {"value": round(value, 3), "unit": "MLUPS", "cores": cpu_cores(),
+            "kind": "oracle", "single_core_value": round(slab.cells * n1 / el1 / 1e6, 3),
             "sample": f"FP64 oracle, z-slab {size}x{size}x{slab.dz} through the centre of the "
-                      f"{size}^3 sphere workload, {n} lattice updates in {el:.1f} s"}
+                      f"{size}^3 sphere workload, {n} lattice updates in {el:.1f} s "
+                      f"({n1} in {el1:.1f} s on one core)"}
 
 
 def run_reference(args, rank, world):
@@ -610,6 +654,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-updates", type=float, default=2)
+    ap.add_argument("--section", default="all", choices=["all", "adjoint_probe"],
+                    help="adjoint_probe: only the above-L2 adjoint measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -618,6 +664,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.section == "adjoint_probe":
+        import torch
+        from paper_2510_11042_gb300 import build as lib_build
+        lib_build.build()
+        print(json.dumps(_adjoint_probe_3d(torch.device("cuda", local_rank))), flush=True)
         return
     if world > 1:
         import torch

@@ -74,6 +74,7 @@ def lib():
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _LIB.orc_stream.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_void_p]
         _LIB.orc_stream_adjoint.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_void_p, ctypes.c_void_p]
+        _LIB.orc_set_threads.argtypes = [ctypes.c_int]
         _LIB.orc_energy.restype = ctypes.c_double
         _LIB.orc_energy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p]
@@ -114,6 +115,11 @@ def collide_cell(f, eps=1.0, mu=1.0):
     out = np.zeros(NQ)
     lib().orc_collide_cell(f.ctypes.data, float(eps), float(mu), out.ctypes.data)
     return out
+
+
+def set_threads(n):
+    """Number of OpenMP threads the oracle's loops use (results do not change)."""
+    lib().orc_set_threads(int(n))
 
 
 def collide_adjoint_cell(m, eps=1.0, mu=1.0):

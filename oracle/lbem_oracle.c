@@ -38,6 +38,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_NQ 42
 
@@ -451,6 +454,17 @@ void orc_stream_adjoint(const orc_params *p, const double *nu, double *out)
                     out[s * ORC_NQ + (fam * 7 + i) * 3 + a] += nu[cell * ORC_NQ + (fam * 7 + i) * 3 + a];
             }
     }
+}
+
+/* Threads of the OpenMP loops (timing the oracle on one core); no effect
+ * without OpenMP.  Does not change any result. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 int orc_abi_version(void) { return 2; }

@@ -28,7 +28,8 @@
 //
 // S^T as a gather: cell x receives mu_i from x + c_i when that cell exists,
 // and its own mu_i where the clamp maps x - c_i back onto x (x on the face
-// that c_i points away from).
+// that c_i points away from).  The gradient term of a step is formed in FP32
+// (A and D^F are FP32) and summed over the steps in FP64.
 #include <algorithm>
 
 #include "lbem_internal.cuh"
@@ -38,8 +39,16 @@ namespace {
 
 constexpr int kAdjBX = 128;
 
+// The adjoint populations use the forward state's FP32 grouped layout
+// (pop_index): per direction, pairs of values per cell (and a single in 2D),
+// each group starting at plane slot i * NC + s0, so a group is one float2 load.
+__device__ __forceinline__ float2 ld_pair(const float *p, int k)
+{
+    return __ldg(reinterpret_cast<const float2 *>(p) + k);
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kAdjBX) adjoint_step_kernel(const AdjointArgs a)
+__global__ void __launch_bounds__(kAdjBX, MODE == 2 ? 7 : 1) adjoint_step_kernel(const AdjointArgs a)
 {
     using PL = Planes<MODE>;
     using M = Mode<MODE>;
@@ -69,7 +78,28 @@ __global__ void __launch_bounds__(kAdjBX) adjoint_step_kernel(const AdjointArgs 
     if (a.nz > 1) d = min(d, min(z, a.nz - 1 - z));
     const float keep = layer_keep(d, a.w, a.sigma_max, a.inv_w);
 
+    constexpr int NC = PL::NC;
     float m[Q];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const float *const *g = a.lin_q + i * NC;
+#pragma unroll
+        for (int s0 = 0; s0 + 1 < NC; s0 += 2) {
+            float2 v = has_nb[i] ? ld_pair(g[s0], nb[i]) : make_float2(0.f, 0.f);
+            if (self[i]) {
+                const float2 w = ld_pair(g[s0], c);
+                v.x += w.x;
+                v.y += w.y;
+            }
+            m[slot_plane(MODE, i, s0)] = keep * v.x;
+            m[slot_plane(MODE, i, s0 + 1)] = keep * v.y;
+        }
+        if (NC & 1) {
+            float v = has_nb[i] ? __ldg(g[NC - 1] + nb[i]) : 0.f;
+            if (self[i]) v += __ldg(g[NC - 1] + c);
+            m[slot_plane(MODE, i, NC - 1)] = keep * v;
+        }
+    }
     float me[7][3], mh[7][3];
 #pragma unroll
     for (int i = 0; i < 7; ++i)
@@ -77,12 +107,8 @@ __global__ void __launch_bounds__(kAdjBX) adjoint_step_kernel(const AdjointArgs 
         for (int k = 0; k < 3; ++k) me[i][k] = mh[i][k] = 0.f;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int i = PL::dir(q);
-        float v = has_nb[i] ? __ldg(a.lin_q[q] + nb[i]) : 0.f;
-        if (self[i]) v += __ldg(a.lin_q[q] + c);
-        m[q] = keep * v;
-        if (PL::fam(q) == 0) me[i][PL::comp(q)] = m[q];
-        else mh[i][PL::comp(q)] = m[q];
+        if (PL::fam(q) == 0) me[PL::dir(q)][PL::comp(q)] = m[q];
+        else mh[PL::dir(q)][PL::comp(q)] = m[q];
     }
 
     float sE[3] = {0.f, 0.f, 0.f}, sH[3] = {0.f, 0.f, 0.f};
@@ -128,18 +154,27 @@ __global__ void __launch_bounds__(kAdjBX) adjoint_step_kernel(const AdjointArgs 
         for (int k = 0; k < PL::NH; ++k) Bv[M::hc(k)] += (float)(a.dft_scale * dx[PL::NE + k]);
     }
 
-    double gs = 0.0;
+    // this step's term in FP32 (its factors are FP32), the sum over steps in FP64
+    float gs = 0.f;
 #pragma unroll
-    for (int k = 0; k < PL::NE; ++k)
-        gs += (double)A[M::ec(k)] * (double)__ldg(a.rec + (long long)k * a.P + c);
-    a.grad[c] += gs;
+    for (int k = 0; k < PL::NE; ++k) gs = fmaf(A[M::ec(k)], __ldg(a.rec + (long long)k * a.P + c), gs);
+    a.grad[c] += (double)gs;
 
     const float beta = __ldg(a.inv_eps + c);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int k = PL::comp(q);
         const float v = PL::fam(q) == 0 ? fmaf(beta, A[k], 2.f * me[0][k]) : Bv[k];
-        a.lout_q[q][c] = v - m[q];
+        m[q] = v - m[q];
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        float *const *g = a.lout_q + i * NC;
+#pragma unroll
+        for (int s0 = 0; s0 + 1 < NC; s0 += 2)
+            reinterpret_cast<float2 *>(g[s0])[c] =
+                make_float2(m[slot_plane(MODE, i, s0)], m[slot_plane(MODE, i, s0 + 1)]);
+        if (NC & 1) g[NC - 1][c] = m[slot_plane(MODE, i, NC - 1)];
     }
 }
 

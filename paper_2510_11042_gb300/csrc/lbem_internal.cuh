@@ -330,7 +330,9 @@ cudaError_t launch_energy(int mode, int storage, const void *f, const float *inv
 // One backward step of the discrete adjoint (adjoint.cu).  lin_q holds
 // mu(t+1) = dJ/du(t+1), the objective's sensitivity to the pulled populations
 // of the next step; the kernel writes mu(t) and adds this step's term of
-// dJ/d(1/eps_r) to grad.  FP32 populations; FP64 gradient accumulator.
+// dJ/d(1/eps_r) to grad.  FP32 populations in the grouped layout of the
+// forward state (lin_q[q'] / lout_q[q'] start plane slot q', as fin_q / fout_q
+// do); FP64 gradient accumulator.
 struct AdjointArgs {
     const float *lin_q[kMaxQ];
     float *lout_q[kMaxQ];
