@@ -272,6 +272,7 @@ def run_gpu(args, rank, world, local_rank):
     K, Wm = args.steps, args.warmup
     main = one_storage("f32", K, Wm, True)
     probe_2d = None if (args.no_batch or world > 1) else run_probe_2d(dev)
+    variants_3d = None if (args.no_batch or world > 1) else run_variants_3d(dev)
     batched = None if (args.no_batch or world > 1) else run_batched(dev)
     adjoint = None if (args.no_adjoint or world > 1) else run_adjoint(dev)
     secondary = {}
@@ -334,6 +335,8 @@ def run_gpu(args, rank, world, local_rank):
     }
     if probe_2d:
         line["bandwidth_probe_2d"] = probe_2d
+    if variants_3d:
+        line["kernel_variants_3d"] = variants_3d
     if batched:
         line["batched"] = batched
     if adjoint:
@@ -449,6 +452,46 @@ def run_probe_2d(dev, n=4096, updates=60):
         gbs = bc * n * n / (ms / 1e3) / 1e9
         out[st] = {"kernel_ms": round(ms, 4), "mlups": round(n * n / (ms / 1e3) / 1e6, 1),
                    "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------------------------ other step-kernel instantiations
+def run_variants_3d(dev, updates=45):
+    """The step kernel's other instantiations on the 384^3 sphere, FP32: with a
+    mu_r map (mu_r = 2 in the sphere; 4 more bytes per cell for 1/mu_r) and with
+    the closed-form source at 30 degrees (every total-field cell evaluates the
+    plane wave in FP64, so this one is not bound by HBM on this part)."""
+    import dataclasses
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    p = W.sphere_problem()
+    cells = int(np.prod(p.shape))
+    hbm, _ = peaks()
+    th = math.radians(30.0)
+    oblique = dataclasses.replace(p.wave, direction=(math.sin(th), 0.0, math.cos(th)),
+                                  polarization=(math.cos(th), 0.0, -math.sin(th)), analytic=True,
+                                  origin=tuple(float(v) for v in p.wave.tf_lo))
+    out = {"workload": "sphere 384^3 (the bench workload), FP32 storage"}
+    for name, mu, wave, bc in (("magnetic_mu2", True, p.wave, b_cell("3d", "f32") + 4),
+                               ("closed_form_source_30deg", False, oblique, b_cell("3d", "f32") + 4)):
+        s = lbem.Solver(p.shape, p.eps, "3d", "f32", p.absorber_width, p.sigma_max, device=dev)
+        if mu:
+            s.set_permeability(np.where(p.eps > 1.0, np.float32(2.0), np.float32(1.0)))
+        s.inject(wave)
+        s.step(5)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(s.stream)
+        s.step(updates)
+        ev[1].record(s.stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / updates
+        gbs = bc * cells / (ms / 1e3) / 1e9
+        out[name] = {"kernel_ms": round(ms, 4), "mlups": round(cells / (ms / 1e3) / 1e6, 1),
+                     "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
         s.close()
         del s
         torch.cuda.empty_cache()

@@ -30,6 +30,8 @@ struct lbem_ctx {
     int cur = 0;
     float *inv_eps = nullptr;
     float *inv_mu = nullptr;    // 1/mu_r plane (1 where no map is set); read when mu_on or analytic
+    float2 *pw_ph = nullptr;    // analytic source: per-axis phase factors, then 3 k_a (p - r0_a)
+    float *pw_d = nullptr;
     bool mu_on = false;
     bool analytic = false;      // the plane wave is the closed-form source, not the line
     PlaneWaveA pw;
@@ -107,7 +109,7 @@ static int check_status(lbem_ctx *h)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t f0, f1, inv_eps, inv_mu, line0, line1, line2, dft, line_dft, scratch, stage, flag, total;
+    size_t f0, f1, inv_eps, inv_mu, pw_tab, line0, line1, line2, dft, line_dft, scratch, stage, flag, total;
     int Q, nxp, n_line_max;
     long long P, ncell;
     size_t elem, dft_doubles_max, scratch_doubles;
@@ -156,6 +158,7 @@ static Layout make_layout(const lbem_grid_desc *g)
     L.f1 = take((size_t)L.Q * L.P * L.elem);
     L.inv_eps = take((size_t)L.P * 4);
     L.inv_mu = take((size_t)L.P * 4);
+    L.pw_tab = take((size_t)(g->nx + g->ny + g->nz) * 12);
     L.line0 = take((size_t)L.Q * L.n_line_max * 4);
     L.line1 = take((size_t)L.Q * L.n_line_max * 4);
     L.line2 = take((size_t)L.Q * L.n_line_max * 4);
@@ -238,7 +241,13 @@ static void fill_common_args(lbem_ctx *h, StepArgs &a)
     a.tfsf = h->analytic ? 2 : 1;
     a.line_on = h->analytic ? 0 : 1;
     a.pw = h->pw;
-    if (h->analytic) a.inv_mu = h->inv_mu;
+    if (h->analytic) {
+        a.inv_mu = h->inv_mu;
+        a.pw_ph = h->pw_ph;
+        a.pw_d = h->pw_d;
+        a.pw_amp = (float)h->pw.amp;
+        a.pw_t_ramp = (float)h->pw.t_ramp;
+    }
     for (int k = 0; k < 3; ++k) {
         a.tf_lo[k] = h->wave.tfsf_lo[k];
         a.tf_hi[k] = h->wave.tfsf_hi[k];
@@ -343,6 +352,8 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->f[1] = h->ws + L.f1;
     h->inv_eps = (float *)(h->ws + L.inv_eps);
     h->inv_mu = (float *)(h->ws + L.inv_mu);
+    h->pw_ph = (float2 *)(h->ws + L.pw_tab);
+    h->pw_d = (float *)(h->pw_ph + (grid->nx + grid->ny + grid->nz));
     h->line[0] = (float *)(h->ws + L.line0);
     h->line[1] = (float *)(h->ws + L.line1);
     h->line[2] = (float *)(h->ws + L.line2);
@@ -583,6 +594,23 @@ static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w)
     p.amp = w->amplitude;
     p.omega = h->omega;
     p.t_ramp = w->ramp_periods * h->T;
+    // per-axis tables of the step kernel (FP64 here, FP32 there)
+    {
+        const int ntab = n3[0] + n3[1] + n3[2];
+        std::vector<float2> ph(ntab);
+        std::vector<float> dd(ntab);
+        int o = 0;
+        for (int ax = 0; ax < 3; ++ax)
+            for (int q = 0; q < n3[ax]; ++q, ++o) {
+                const double d = 3.0 * p.k[ax] * ((double)q - p.r0[ax]);
+                const double psi = std::fmod(h->omega * d, 2.0 * M_PI);
+                ph[o] = make_float2((float)std::cos(psi), (float)-std::sin(psi));
+                dd[o] = (float)d;
+            }
+        CK(h, cudaMemcpyAsync(h->pw_ph, ph.data(), ntab * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->pw_d, dd.data(), ntab * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     if (ntff) {
         build_faces(h);
     } else {
@@ -634,6 +662,13 @@ int32_t lbem_step(lbem_handle h, int64_t n)
                 source_fields(h, h->t + 2, a.src_E, a.src_H);
             }
             a.tn = h->t;
+            if (h->analytic)
+                for (int k = 0; k < 2; ++k) {
+                    const int64_t ts = h->t + k;
+                    const double ph = 2.0 * M_PI * (double)(ts % h->T) / (double)h->T;  // w t_s mod 2 pi
+                    a.pw_wt[k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+                    a.pw_t[k] = (float)ts;
+                }
             a.dft_on = (h->faces.nfaces > 0 && h->dft_t0 >= 1 && t >= h->dft_t0 &&
                         t < h->dft_t0 + (int64_t)h->dft_periods * h->T);
             if (a.dft_on) {

@@ -192,6 +192,15 @@ struct StepArgs {
     int tfsf;
     PlaneWaveA pw;
     long long tn;
+    // analytic source in FP32 (kind 2): per-axis tables over the grid
+    // coordinates, concatenated x, y, z: pw_ph[p] = exp(-j w 3 k_a (p - r0_a)),
+    // pw_d[p] = 3 k_a (p - r0_a); pw_wt[s] = exp(j w t_s) and pw_t[s] = t_s for
+    // t_0 = n (pulled cells) and t_1 = n + 1 (the cell itself)
+    const float2 *pw_ph;
+    const float *pw_d;
+    float2 pw_wt[2];
+    float pw_t[2];
+    float pw_amp, pw_t_ramp;
     int tf_lo[3], tf_hi[3];
     int inc_axis;
     const float *line_n;

@@ -173,6 +173,27 @@ __device__ __forceinline__ void line_work(const StepArgs &a, int s)
 // reads, clamp(r - c_i), at time n.  (Storing G = F - I inside the box, the
 // link-wise rule F_pulled = G_pulled + chi(r) I_pulled makes
 // G* = keep C(G_pulled) + chi(r) [keep C(I_pulled) - I(r, n+1)].)
+// Amplitude E0 ramp(tau) sin(w tau) of the closed-form wave at cell (px, py, pz)
+// and time t_s, tau = t_s - 3 k.(p - r0), from the per-axis tables in FP32:
+// sin(w tau) = Im(exp(j w t_s) prod_a exp(-j w 3 k_a (p_a - r0_a))).  All
+// factors have unit modulus, so the phase carries no growing rounding error;
+// tau (only needed during the ramp) is formed from small terms.
+__device__ __forceinline__ float pw_amp_tab(const StepArgs &a, int px, int py, int pz, int s)
+{
+    const float2 fx = __ldg(a.pw_ph + px), fy = __ldg(a.pw_ph + a.nx + py),
+                 fz = __ldg(a.pw_ph + a.nx + a.ny + pz);
+    const float2 fxy = make_float2(fx.x * fy.x - fx.y * fy.y, fx.x * fy.y + fx.y * fy.x);
+    const float2 f = make_float2(fxy.x * fz.x - fxy.y * fz.y, fxy.x * fz.y + fxy.y * fz.x);
+    const float2 w = a.pw_wt[s];
+    const float sn = w.x * f.y + w.y * f.x;
+    const float tau = a.pw_t[s] - (__ldg(a.pw_d + px) + __ldg(a.pw_d + a.nx + py) +
+                                   __ldg(a.pw_d + a.nx + a.ny + pz));
+    float ramp = 1.f;
+    if (tau <= 0.f) ramp = 0.f;
+    else if (tau < a.pw_t_ramp) ramp = 0.5f * (1.f - cospif(tau / a.pw_t_ramp));
+    return a.pw_amp * ramp * sn;
+}
+
 template <int MODE>
 __device__ __forceinline__ void analytic_source(const StepArgs &a, int x, int y, int z, float inv_eps,
                                                 float inv_mu, float keep, float *src)
@@ -180,7 +201,6 @@ __device__ __forceinline__ void analytic_source(const StepArgs &a, int x, int y,
     using PL = Planes<MODE>;
     constexpr int Q = PL::Q;
     constexpr float sixth = 1.0f / 6.0f;
-    const double t = (double)a.tn;
     const float pol[3] = {(float)a.pw.pol[0], (float)a.pw.pol[1], (float)a.pw.pol[2]};
     const float kxp[3] = {(float)a.pw.kxp[0], (float)a.pw.kxp[1], (float)a.pw.kxp[2]};
     float amp[7];
@@ -190,7 +210,7 @@ __device__ __forceinline__ void analytic_source(const StepArgs &a, int x, int y,
         const int px = min(max(x - (d == 0 ? sg : 0), 0), a.nx - 1);
         const int py = min(max(y - (d == 1 ? sg : 0), 0), a.ny - 1);
         const int pz = min(max(z - (d == 2 ? sg : 0), 0), a.nz - 1);
-        amp[i] = (float)pw_amplitude(a.pw, px, py, pz, t);
+        amp[i] = pw_amp_tab(a, px, py, pz, 0);
     }
     float D[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -212,7 +232,7 @@ __device__ __forceinline__ void analytic_source(const StepArgs &a, int x, int y,
         E3[c] = third(E[c]);
         H3[c] = third(H[c]);
     }
-    const float an = (float)pw_amplitude(a.pw, x, y, z, t + 1.0);
+    const float an = pw_amp_tab(a, x, y, z, 1);
     const float En[3] = {an * pol[0], an * pol[1], an * pol[2]};
     const float Hn[3] = {an * kxp[0], an * kxp[1], an * kxp[2]};
 #pragma unroll
