@@ -274,6 +274,13 @@ int32_t lbem_batch_run(lbem_batch b, const int64_t *steps, int32_t autotune);
 int32_t lbem_batch_config(lbem_batch b, int32_t *blocks_per_sm, int32_t *rows_per_item,
                           double *ms_per_step, int32_t *split);
 int64_t lbem_batch_launches(lbem_batch b);
+/* Failure-path check of the batched kernel's bounded grid barrier (no
+ * counterpart in the paper): one block waits at the barrier for an arrival
+ * that never comes.  Its wait gives up after about a second and reports
+ * through the status word, as a real stall would; the call then returns
+ * LBEM_ERR_TIMEOUT with the same message lbem_batch_run gives, and the batch
+ * and its handles stay usable.  Any other return is a fault of the check. */
+int32_t lbem_batch_selftest_barrier(lbem_batch b);
 const char *lbem_batch_last_error(lbem_batch b);
 void lbem_batch_destroy(lbem_batch b);
 

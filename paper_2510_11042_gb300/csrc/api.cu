@@ -1005,6 +1005,27 @@ extern "C" int32_t lbem_batch_config(lbem_batch b, int32_t *blocks_per_sm, int32
     return LBEM_OK;
 }
 
+extern "C" int32_t lbem_batch_selftest_barrier(lbem_batch b)
+{
+    if (!b) return bfail(nullptr, LBEM_ERR_ARG, "NULL batch");
+    if (cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned) + sizeof(int), b->stream) != cudaSuccess)
+        return bfail(b, LBEM_ERR_CUDA, "barrier reset failed");
+    BatchArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.bar_count = b->bar;
+    a.bar_gen = b->bar + 1;
+    a.status = b->status;
+    if (launch_barrier_selftest(a, b->stream) != cudaSuccess)
+        return bfail(b, LBEM_ERR_CUDA, "self-test launch: %s", cudaGetErrorString(cudaGetLastError()));
+    b->launches += 1;
+    int st = 0;
+    if (cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return bfail(b, LBEM_ERR_CUDA, "self-test: %s", cudaGetErrorString(cudaGetLastError()));
+    if (st & 2) return bfail(b, LBEM_ERR_TIMEOUT, "a grid-barrier wait of the batched kernel ran out");
+    return bfail(b, LBEM_ERR_STATE, "the barrier self-test's wait did not run out");
+}
+
 extern "C" int64_t lbem_batch_launches(lbem_batch b) { return b ? b->launches : 0; }
 
 extern "C" const char *lbem_batch_last_error(lbem_batch b) { return b ? b->err : g_create_err; }

@@ -261,6 +261,7 @@ struct BatchArgs {
 
 // Launchers (step.cu)
 cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cudaStream_t s);
+cudaError_t launch_barrier_selftest(const BatchArgs &b, cudaStream_t s);
 int batch_max_blocks_per_sm(int mode, int storage);
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
 // The step kernel with a per-cell mu_r (a.inv_mu), Eq. 2's h_0 = (mu_r - 1) H

@@ -754,6 +754,17 @@ int max_blocks_t()
 
 }  // namespace
 
+// Failure-path check of the bounded grid barrier: one block waits for an
+// arrival that never comes, gives up after the bounded number of polls, sets
+// status bit 1 and returns.
+__global__ void barrier_selftest_kernel(const BatchArgs b) { grid_barrier(b, gridDim.x + 1); }
+
+cudaError_t launch_barrier_selftest(const BatchArgs &b, cudaStream_t s)
+{
+    barrier_selftest_kernel<<<1, kBX, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cudaStream_t s)
 {
     switch (mode * 3 + storage) {

@@ -95,6 +95,7 @@ _SIGS = {
     "lbem_batch_config": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I32)]),
     "lbem_batch_launches": (_I64, [_P]),
+    "lbem_batch_selftest_barrier": (_I32, [_P]),
     "lbem_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbem_batch_destroy": (None, [_P]),
     "lbem_adjoint_workspace_bytes": (_I32, [_P, _I64, _I32, ctypes.POINTER(ctypes.c_size_t)]),
@@ -351,6 +352,12 @@ def lbem_batch_config(b):
     _bcheck(lib().lbem_batch_config(b, ctypes.byref(bps), ctypes.byref(rpi), ctypes.byref(ms),
                                     ctypes.byref(split)), b)
     return bps.value, rpi.value, ms.value, bool(split.value)
+
+
+def lbem_batch_selftest_barrier(b):
+    """Make the batched kernel's bounded barrier wait run out; raises LbemError
+    (LBEM_ERR_TIMEOUT is the expected outcome)."""
+    _bcheck(lib().lbem_batch_selftest_barrier(b), b)
 
 
 def lbem_batch_launches(b) -> int:

@@ -74,3 +74,26 @@ def test_batch_with_large_grid(schedule):
         assert s2.time == p.steps
         assert rel_l2(s2.populations(), s1.populations()) <= 1e-6
     batch.close()
+
+
+def test_bounded_barrier_wait_reports_timeout_and_context_survives():
+    """Failure detection without a GPU fault: one block waits at the batched
+    kernel's grid barrier for an arrival that never comes; the bounded wait
+    gives up (about a second), the call reports LBEM_ERR_TIMEOUT, and the same
+    batch then runs correctly."""
+    import time
+    from paper_2510_11042_gb300 import lbem
+    probs = problems()[:2]
+    singles = [gpu_solver(p) for p in probs]
+    batched = [gpu_solver(p, steps=0) for p in probs]
+    batch = lbem.Batch(batched)
+    t0 = time.perf_counter()
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_batch_selftest_barrier(batch.b)
+    assert e.value.code == lbem.LBEM_ERR_TIMEOUT
+    assert "ran out" in str(e.value)
+    assert time.perf_counter() - t0 < 30.0
+    batch.run([p.steps for p in probs], autotune=False)
+    for p, s1, s2 in zip(probs, singles, batched):
+        assert rel_l2(s2.populations(), s1.populations()) <= 1e-6
+    batch.close()
