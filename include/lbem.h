@@ -233,8 +233,9 @@ int32_t lbem_get_dft(lbem_handle h, double *out_host);
  * population is NaN or Inf. */
 int32_t lbem_energy(lbem_handle h, double *out_host);
 
-/* Checkpoint: opaque snapshot of populations, incident line, DFT accumulators
- * and time, for the same grid description. */
+/* Checkpoint: opaque snapshot of populations, incident line, DFT accumulators,
+ * time and storage scale, for the same grid description (the plane wave and
+ * the permittivity are not part of it: set them as for the saved run). */
 int32_t lbem_state_bytes(lbem_handle h, size_t *bytes_out);
 int32_t lbem_save_state(lbem_handle h, void *buf_host, size_t bytes);
 int32_t lbem_load_state(lbem_handle h, const void *buf_host, size_t bytes);

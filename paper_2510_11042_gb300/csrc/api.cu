@@ -1259,6 +1259,8 @@ struct StateHeader {
     int32_t nx, ny, nz, mode, storage, Q;
     int64_t t;
     int64_t pop_bytes, line_bytes, line_dft_bytes, dft_bytes;
+    float scale;            // storage scale the populations are stored with
+    int32_t pad;
 };
 
 int32_t lbem_state_bytes(lbem_handle h, size_t *bytes)
@@ -1277,7 +1279,8 @@ int32_t lbem_save_state(lbem_handle h, void *buf, size_t bytes)
     if (bytes < need) return fail(h, LBEM_ERR_ARG, "buffer of %zu bytes < %zu", bytes, need);
     StateHeader hd;
     std::memset(&hd, 0, sizeof hd);
-    std::memcpy(hd.magic, "LBEMSTA1", 8);
+    std::memcpy(hd.magic, "LBEMSTA2", 8);
+    hd.scale = h->scale;
     hd.nx = h->g.nx; hd.ny = h->g.ny; hd.nz = h->g.nz; hd.mode = h->g.mode; hd.storage = h->g.storage;
     hd.Q = h->Q;
     hd.t = h->t;
@@ -1309,7 +1312,7 @@ int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
     if (bytes < need) return fail(h, LBEM_ERR_ARG, "buffer of %zu bytes < %zu", bytes, need);
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof hd);
-    if (std::memcmp(hd.magic, "LBEMSTA1", 8) || hd.nx != h->g.nx || hd.ny != h->g.ny || hd.nz != h->g.nz ||
+    if (std::memcmp(hd.magic, "LBEMSTA2", 8) || hd.nx != h->g.nx || hd.ny != h->g.ny || hd.nz != h->g.nz ||
         hd.mode != h->g.mode || hd.storage != h->g.storage || hd.Q != h->Q)
         return fail(h, LBEM_ERR_ARG, "snapshot does not match this grid");
     h->adj_valid = false;
@@ -1326,6 +1329,8 @@ int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
     CK(h, cudaMemcpyAsync(h->dft, p, hd.dft_bytes, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->t = hd.t;
+    h->scale = hd.scale;
+    h->inv_scale = 1.0f / hd.scale;
     return LBEM_OK;
 }
 

@@ -258,3 +258,32 @@ def test_high_contrast_parity_and_stability():
         energies.append(sc.energy())
     assert all(np.isfinite(energies))
     assert max(energies[3:]) <= 2.0 * max(energies[:3])   # steady state, no growth
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_storage_scale_and_checkpoint_in_grouped_16bit_layout(storage):
+    """lbem_set_storage_scale rescales the stored state in place (the state keeps
+    its value to 16-bit rounding); a 3D checkpoint of 16-bit storage continues
+    bit for bit."""
+    from paper_2510_11042_gb300 import lbem
+    p = W.sphere_problem(n=40, x=2.0, wavelength=8.0, eps_in=2.25, w=6, periods=4, gap_ntff=2, gap_tf=2)
+    init = W.random_state("3d", p.shape, 31)
+    s = gpu_solver(p, storage=storage, init=init, steps=30)
+    before = s.populations()
+    old = lbem.lbem_get_storage_scale(s.h)
+    lbem.lbem_set_storage_scale(s.h, old * 4.0)
+    assert lbem.lbem_get_storage_scale(s.h) == old * 4.0
+    after = s.populations()
+    tol = 1e-3 if storage == "f16" else 8e-3
+    assert rel_l2(after, before) <= tol
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_set_storage_scale(s.h, 3.0)
+    assert e.value.code == lbem.LBEM_ERR_ARG
+    snap = lbem.lbem_save_state(s.h)
+    s.step(20)
+    ref = s.populations()
+    t = gpu_solver(p, storage=storage, steps=0)
+    lbem.lbem_load_state(t.h, snap)              # restores the scale too
+    assert lbem.lbem_get_storage_scale(t.h) == old * 4.0
+    t.step(20)
+    np.testing.assert_array_equal(t.populations(), ref)
