@@ -556,17 +556,20 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
     store_cell<MODE, S>(a, c, f);
 }
 
-// One block per tile of BX cells x rows_of<S> consecutive rows (y fastest,
-// then z); the first blocks also update the incident line.  Blocks of several
-// rows cut the per-block start-up cost of short 128-cell rows; 72 registers
-// (7 blocks of 128 threads per SM) hold a cell without spilling.  Both were
-// chosen by timing the 384^3 sphere on GB300.
+// One block per tile of BX cells x R consecutive rows (y fastest, then z);
+// the first blocks also update the incident line.  R = rows_of<S> blocks of
+// several rows cut the per-block start-up cost of short 128-cell rows; grids
+// of under one wave of such blocks (152 SMs x 7) take one row per block
+// instead (ONE), so that every SM gets work.  72 registers (7 blocks of 128
+// threads per SM) hold a cell without spilling.  These were chosen by timing
+// the 384^3 sphere and 256^2 to 4096^2 EZ grids on GB300.
 template <class S> __host__ __device__ constexpr int rows_of() { return sizeof(S) == 4 ? 2 : 4; }
+constexpr long long kWaveBlocks = 152LL * 7;
 
-template <int MODE, class S, int BX, bool REC = false, bool MU = false, bool ANA = false>
+template <int MODE, class S, int BX, bool REC = false, bool MU = false, bool ANA = false, bool ONE = false>
 __global__ void __launch_bounds__(BX, 7) step_kernel_cell(const StepArgs a)
 {
-    constexpr int R = rows_of<S>();
+    constexpr int R = ONE ? 1 : rows_of<S>();
     const int b = blockIdx.x;
     if (a.line_on) {
         const int s = b * BX + threadIdx.x;
@@ -728,12 +731,16 @@ cudaError_t launch_cell(StepArgs a, cudaStream_t s)
 {
     a.nblk_x = (a.nx + kBX - 1) / kBX;
     a.rows_per_block = rows_of<S>();
+    if ((long long)a.nblk_x * a.ny * a.nz / a.rows_per_block < kWaveBlocks) a.rows_per_block = 1;
     a.nblk_main = a.nblk_x * ((a.ny * a.nz + a.rows_per_block - 1) / a.rows_per_block);
     if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
     if (REC && a.rec == nullptr) return cudaErrorInvalidValue;
     if (MU && a.inv_mu == nullptr) return cudaErrorInvalidValue;
     if (ANA != (a.tfsf == 2)) return cudaErrorInvalidValue;
-    step_kernel_cell<MODE, S, kBX, REC, MU, ANA><<<a.nblk_main, kBX, 0, s>>>(a);
+    if (a.rows_per_block == 1)
+        step_kernel_cell<MODE, S, kBX, REC, MU, ANA, true><<<a.nblk_main, kBX, 0, s>>>(a);
+    else
+        step_kernel_cell<MODE, S, kBX, REC, MU, ANA, false><<<a.nblk_main, kBX, 0, s>>>(a);
     return cudaGetLastError();
 }
 

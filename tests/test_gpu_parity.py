@@ -155,6 +155,43 @@ def test_edge_shapes_without_source(mode, shape):
     assert rel_l2(s.populations(), oracle_to_planes(lat.f, mode, shape)) <= TOL
 
 
+# Per-row bounds: a row that a block skips keeps its initial state, an O(1)
+# error; the FP16/BF16 bounds sit well above their rounding (2^-11, 2^-8 per
+# value over 9 steps).
+_ROW_BOUND = {"f32": 1e-4, "f16": 2e-2, "bf16": 1e-1}
+
+
+@pytest.mark.parametrize("mode,shape,storage", [
+    ("ez", (260, 700, 1), "f32"),    # 3 x 700 / 2 = 1050 blocks: under one wave, one row per block
+    ("ez", (260, 1001, 1), "f32"),   # 1501 blocks of 2 rows, odd row count
+    ("hz", (130, 2131, 1), "bf16"),  # 1065 blocks of 4 rows, 3-row tail
+    ("3d", (33, 45, 51), "f32"),     # 1147 blocks of 2 rows, odd row count
+    ("3d", (70, 67, 69), "f16"),     # 1155 blocks of 4 rows, 3-row tail
+])
+def test_row_blocking_on_both_sides_of_one_wave(mode, shape, storage):
+    """Grids just above and below one wave of multi-row blocks (152 SMs x 7
+    blocks) take the multi-row and the one-row instantiation of the step
+    kernel; every row of either must be updated once per step."""
+    eps = W.random_eps(shape, 1.0, 6.0, 21)
+    p = W.Problem("rows", mode, shape, eps, 4, 0.3, None, 9, 1)
+    init = W.random_state(mode, shape, 22)
+    s = gpu_solver(p, storage=storage, init=init, steps=0)
+    s.step(9)
+    from oracle import lb
+    lat = lb.Lattice(shape, eps, sponge_w=4, sigma_max=0.3)
+    lat.f = planes_to_oracle(init.astype(np.float64), mode)
+    for n in range(9):
+        lat.step(n)
+    got = np.asarray(s.populations(), np.float64)
+    exp = oracle_to_planes(lat.f, mode, shape)
+    if storage == "f32":
+        assert rel_l2(got, exp) <= TOL
+    num = np.sqrt(((got - exp) ** 2).sum(axis=(0, 3)))
+    den = np.sqrt((exp ** 2).sum(axis=(0, 3)))
+    row_err = num / np.maximum(den, 1e-30)
+    assert row_err.max() <= _ROW_BOUND[storage], (row_err.max(), np.unravel_index(row_err.argmax(), row_err.shape))
+
+
 def test_checkpoint_round_trip_and_energy():
     p = W.cylinder_problem(n=96, x=3.0, wavelength=12.0, eps_in=3.0, w=8, mode="ez", periods=6)
     from paper_2510_11042_gb300 import lbem
