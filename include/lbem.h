@@ -195,7 +195,11 @@ int32_t lbem_set_permeability(lbem_handle h, const float *mu_r, int32_t mu_on_de
  * |E_I| the incident line's E phasor along pol at the centre (Eq. 5/6: "in the
  * vicinity of the scatterer").  theta_host, phi_host: n angles (phi ignored
  * and may be NULL in 2D).  s2_host: n outputs.  amp_host (optional, NULL): 12
- * doubles per angle, Re/Im of N_x, N_y, N_z, L_x, L_y, L_z.  All FP64. */
+ * doubles per angle, Re/Im of N_x, N_y, N_z, L_x, L_y, L_z.  Inputs and
+ * outputs are FP64.  In 2D the projection is FP64 throughout; in 3D it is a
+ * complex FP32 contraction (phasors and FP64-evaluated phases rounded once to
+ * FP32, FP32 sums over at most a chunk of face rows and a 64-column tile, FP64
+ * sums above), deterministic call to call. */
 int32_t lbem_far_field(lbem_handle h, const double *theta_host, const double *phi_host,
                        int32_t n, double *s2_host, double *amp_host);
 

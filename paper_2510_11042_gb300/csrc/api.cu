@@ -42,6 +42,9 @@ struct lbem_ctx {
     double *line_dft = nullptr;
     double *scratch = nullptr;  // far-field partials / energy partials
     size_t scratch_doubles = 0;
+    float2 *x32 = nullptr;      // 3D far field in FP32: packed faces, then phase tables
+    float2 *tab32 = nullptr;
+    size_t x32_cap = 0, tab32_cap = 0;
     float *stage = nullptr;     // one FP32 plane of ncell values
     int *flag = nullptr;
     // time and source
@@ -109,7 +112,8 @@ static int check_status(lbem_ctx *h)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t f0, f1, inv_eps, inv_mu, pw_tab, line0, line1, line2, dft, line_dft, scratch, stage, flag, total;
+    size_t f0, f1, inv_eps, inv_mu, pw_tab, line0, line1, line2, dft, line_dft, scratch, ff32, stage, flag, total;
+    size_t x32_cap, tab32_cap;  // float2 capacities of the 3D FP32 far field (0 in 2D)
     int Q, nxp, n_line_max;
     long long P, ncell;
     size_t elem, dft_doubles_max, scratch_doubles;
@@ -165,6 +169,19 @@ static Layout make_layout(const lbem_grid_desc *g)
     L.dft = take(L.dft_doubles_max * 8);
     L.line_dft = take((size_t)L.n_line_max * 6 * 8);
     L.scratch = take(L.scratch_doubles * 8);
+    // 3D far field in FP32: faces padded to 16 rows x 64 columns (the NTFF box
+    // lies in the grid, so its faces are bounded by the grid's) and phase
+    // tables for a batch of angles
+    L.x32_cap = L.tab32_cap = 0;
+    if (g->mode == 2) {
+        const long long n[3] = {g->nx, g->ny, g->nz};
+        for (int ax = 0; ax < 3; ++ax) {
+            const long long nu = n[ax == 2 ? 1 : 2], nv = n[ax == 0 ? 1 : 0];
+            L.x32_cap += 2 * ((nu + 15) / 16 * 16) * 4 * ((nv + 63) / 64 * 64);
+        }
+        L.tab32_cap = (size_t)(g->nx + g->ny + g->nz) * kAngleBatch;
+    }
+    L.ff32 = take((L.x32_cap + L.tab32_cap) * 8);
     L.stage = take((size_t)L.ncell * 4);
     L.flag = take(256);
     L.total = o;
@@ -363,6 +380,10 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->line_dft = (double *)(h->ws + L.line_dft);
     h->scratch = (double *)(h->ws + L.scratch);
     h->scratch_doubles = L.scratch_doubles;
+    h->x32_cap = L.x32_cap;
+    h->tab32_cap = L.tab32_cap;
+    h->x32 = L.x32_cap ? (float2 *)(h->ws + L.ff32) : nullptr;
+    h->tab32 = L.x32_cap ? h->x32 + L.x32_cap : nullptr;
     h->stage = (float *)(h->ws + L.stage);
     h->flag = (int *)(h->ws + L.flag);
     default_scale(h);
@@ -1058,6 +1079,15 @@ static int far_field_chunks(const FaceGeom &g)
     return (int)std::max<long long>(1, std::min<long long>(kMaxChunks, c));
 }
 
+// The 3D projection runs as an FP32 contraction in the workspace's ff32 region.
+static void set_far_field_f32(lbem_ctx *h, FarFieldArgs &a)
+{
+    a.x32 = h->x32;
+    a.tab32 = h->tab32;
+    a.x32_cap = (long long)h->x32_cap;
+    a.tab32_cap = (long long)h->tab32_cap;
+}
+
 static void centre_nodes(lbem_ctx *h, int *i0, int *i1)
 {
     const double c = h->wave.center[h->inc_axis];
@@ -1106,6 +1136,7 @@ int32_t lbem_far_field(lbem_handle h, const double *theta, const double *phi, in
         a.partial = d_part;
         a.s2 = d_s2;
         a.amp = d_amp;
+        set_far_field_f32(h, a);
         int l = 0;
         CK(h, launch_far_field(a, h->stream, &l));
         h->launches += l;
@@ -1531,6 +1562,7 @@ int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, cons
     fa.partial = d_part;
     fa.s2 = d_s2;
     fa.amp = d_amp;
+    set_far_field_f32(h, fa);
     int l = 0;
     CK(h, launch_far_field(fa, h->stream, &l));
     h->launches += l;

@@ -15,7 +15,7 @@ namespace lbem {
 constexpr int kMaxQ = 42;        // 2 families x 7 directions x 3 components (3D)
 constexpr int kMaxFaces = 6;
 constexpr int kAngleBatch = 1024;  // angles per far-field kernel pass
-constexpr int kMaxChunks = 64;     // face-cell chunks per angle in the projection
+constexpr int kMaxChunks = 128;    // face-cell chunks per angle in the projection
 
 // Per-mode population planes (Sec. 2.1, D3Q7 with 3-vector populations).  A
 // family stores only the vector components that are non-zero in the mode:
@@ -312,6 +312,15 @@ struct FarFieldArgs {
     double *partial;           // [n_ang][chunks][12]
     double *s2;                // [n_ang]
     double *amp;               // [n_ang][12]
+    // 3D FP32 contraction (far_field_f32); x32 == nullptr selects the FP64 kernels
+    float2 *x32;               // packed face phasors [face][nup][4][nvp], weights folded in
+    float2 *tab32;             // phase tables [n0 + n1 + n2][n_ang_pad]
+    long long x32_cap, tab32_cap;  // capacities in float2
+    int n_ang_pad;             // n_ang rounded up to the angle tile
+    int uc;                    // face rows per chunk
+    int nup[kMaxFaces], nvp[kMaxFaces];  // padded rows / columns per face
+    long long off32[kMaxFaces + 1];      // face offsets in x32 (float2)
+    int chunk_start[kMaxFaces + 1];      // first chunk of each face
 };
 cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launches);
 cudaError_t launch_far_field_partial(const FarFieldArgs &a, cudaStream_t s);

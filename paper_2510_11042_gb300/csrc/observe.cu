@@ -554,6 +554,208 @@ inline int grid_for(long long n, int threads)
     return (int)(b < 1 ? 1 : b);
 }
 
+
+// ---------------------------------------------------------------------------
+// 3D far field as an FP32 contraction.  With the phase factorised as above,
+// the projection of face f is, per angle a and tangential component X,
+//   sum_v t_v(a, v) t_w(a) sum_u t_u(a, u) w_u w_v X(u, v),
+// a complex matrix product [angles x u] . [u x (v, X)] followed by a short
+// contraction over v.  GB300's FP64 pipe runs at 1/64 of its FP32 rate, so
+// the FP64 column kernel above spends ~17 ms on a 384^3 sphere's 543 angles.
+// Here the products and the sums over at most uc face rows (and over the 64
+// columns of a tile) are FP32, and everything above that (column tiles, row
+// chunks, faces) is summed in FP64, in a fixed order.  Phases are evaluated in
+// FP64 and rounded once; the phasors are rounded once to FP32.  A term then
+// carries ~2^-23 relative error and a partial FP32 sum of n terms at most
+// n 2^-24 of its absolute sum (n <= uc = 16..512 rows, or 64 columns).
+constexpr int kF32Threads = 256;
+constexpr int kF32Angles = 32;   // angles per block: 8 warps x 4
+constexpr int kF32Cols = 64;     // face columns per tile: 32 lanes x 2
+constexpr int kF32Rows = 16;     // face rows staged in shared memory per pass
+
+// Phase tables tab32[e][a] = exp(j k r_ax(a) (p_e - c_ax)) for the box
+// coordinates p_e along x, y, z (e in [0, n0 + n1 + n2)); zero for padded angles.
+__global__ void ff32_tables(const FarFieldArgs a)
+{
+    const int n0 = a.g.hi[0] - a.g.lo[0] + 1, n1 = a.g.hi[1] - a.g.lo[1] + 1,
+              n2 = a.g.hi[2] - a.g.lo[2] + 1;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)(n0 + n1 + n2) * a.n_ang_pad) return;
+    const int ang = (int)(i % a.n_ang_pad), e = (int)(i / a.n_ang_pad);
+    float2 out = make_float2(0.f, 0.f);
+    if (ang < a.n_ang) {
+        const int ax = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+        const int toff = ax == 0 ? 0 : (ax == 1 ? n0 : n0 + n1);
+        const double th = a.theta[ang], ph = a.phi[ang];
+        const double r = ax == 0 ? sin(th) * cos(ph) : (ax == 1 ? sin(th) * sin(ph) : cos(th));
+        const double pos = a.g.lo[ax] + (e - toff);
+        double sp, cp;
+        sincos(a.k * r * (pos - a.center[ax]), &sp, &cp);
+        out = make_float2((float)cp, (float)sp);
+    }
+    a.tab32[i] = out;
+}
+
+// Packed faces x32[f][u][q][v] = w_u w_v X_q(u, v) in FP32, q = H_b1, H_b2,
+// E_b1, E_b2 (b1 = AX+1, b2 = AX+2 mod 3); zero in the padding.
+__global__ void ff32_pack(const FarFieldArgs a)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.off32[a.g.nfaces]) return;
+    int f = 0;
+    while (i >= a.off32[f + 1]) ++f;
+    const long long r = i - a.off32[f];
+    const int nvp = a.nvp[f];
+    const int v = (int)(r % nvp);
+    const long long t = r / nvp;
+    const int q = (int)(t % 4), u = (int)(t / 4);
+    const int nu = a.g.nu[f], nv = a.g.nv[f];
+    float2 out = make_float2(0.f, 0.f);
+    if (u < nu && v < nv) {
+        const int ax = a.g.axis[f], b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+        const int slot = q == 0 ? slot_H(2, b1) : q == 1 ? slot_H(2, b2) : q == 2 ? slot_E(2, b1) : slot_E(2, b2);
+        const long long plane = (long long)nu * nv;
+        const double *c = a.dft + a.g.off[f] + (long long)u * nv + v;
+        double w = 1.0;
+        if (nu > 1 && (u == 0 || u == nu - 1)) w *= 0.5;
+        if (nv > 1 && (v == 0 || v == nv - 1)) w *= 0.5;
+        out = make_float2((float)(w * c[(2 * slot) * plane]), (float)(w * c[(2 * slot + 1) * plane]));
+    }
+    a.x32[i] = out;
+}
+
+__device__ __forceinline__ void cmac(float &sr, float &si, float2 p, float xr, float xi)
+{
+    sr = fmaf(p.x, xr, fmaf(-p.y, xi, sr));
+    si = fmaf(p.x, xi, fmaf(p.y, xr, si));
+}
+
+// One step of a reduce-scatter over the warp: a lane keeps the half of its
+// values selected by its bit H and adds the partner's copy of that half.
+// After the steps 16, 8, 4, 2, 1, lane l holds the warp's sum of value l.
+template <int H>
+__device__ __forceinline__ void rs_stage(float (&o)[32], int lane)
+{
+    const bool up = (lane & H) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float send = up ? o[i] : o[i + H];
+        const float keep = up ? o[i + H] : o[i];
+        o[i] = keep + __shfl_xor_sync(0xffffffffu, send, H);
+    }
+}
+
+// One block per (tile of 32 angles, chunk of uc rows of one face).  Warp w
+// owns angles 4w..4w+3 of the tile and lane l columns 2l, 2l+1 of each
+// 64-column tile.  Per column tile: FP32 column sums over the chunk's rows,
+// then the column factor, a reduce-scatter over the warp (lane l ends with
+// value l of the warp's 4 angles x 8 outputs), and an FP64 add into shared
+// memory.  Writes partial[angle][chunk][12].
+__global__ void __launch_bounds__(kF32Threads, 2) far_field_f32(const FarFieldArgs a)
+{
+    extern __shared__ float4 ff_sm[];
+    float2 *At = reinterpret_cast<float2 *>(ff_sm);                  // [uc][32] row phases
+    float4 *Xs = ff_sm + a.uc * (kF32Angles / 2);                    // [16 rows x 4 q][32] (2 columns)
+    double *acc = reinterpret_cast<double *>(Xs + kF32Rows * 4 * 32);  // [32 angles][12]
+    const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
+    const int ang0 = blockIdx.x * kF32Angles;
+    const int ch = blockIdx.y;
+    int f = 0;
+    while (f + 1 < a.g.nfaces && ch >= a.chunk_start[f + 1]) ++f;
+    const int u0 = (ch - a.chunk_start[f]) * a.uc;
+    const int nu = a.g.nu[f], nv = a.g.nv[f], nvp = a.nvp[f];
+    const int un = min(a.uc, a.nup[f] - u0);  // a multiple of kF32Rows
+    const int ax = a.g.axis[f];
+    const int ua = ax == 2 ? 1 : 2, va = ax == 0 ? 1 : 0;
+    const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+    const int n0 = a.g.hi[0] - a.g.lo[0] + 1, n1 = a.g.hi[1] - a.g.lo[1] + 1;
+    auto toff = [&](int axis) { return axis == 0 ? 0 : (axis == 1 ? n0 : n0 + n1); };
+    const int eu = toff(ua), ev = toff(va);
+    for (int i = threadIdx.x; i < un * kF32Angles; i += kF32Threads) {
+        const int u = i / kF32Angles, j = i % kF32Angles;
+        At[i] = u0 + u < nu ? a.tab32[(long long)(eu + u0 + u) * a.n_ang_pad + ang0 + j]
+                            : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < kF32Angles * 12; i += kF32Threads) acc[i] = 0.0;
+    const int ew = toff(ax) + (a.g.side[f] ? a.g.hi[ax] - a.g.lo[ax] : 0);
+    const double sgn = a.g.side[f] ? 1.0 : -1.0;
+    const float4 *X = reinterpret_cast<const float4 *>(a.x32 + a.off32[f]);
+    const int nvq = nvp / 2;  // float4 (two columns) per row of one component
+    // output slot of reduce-scatter value q of an angle: J_b1, J_b2, M_b1, M_b2 (re, im)
+    const int qv = lane & 7, jv = lane >> 3;
+    const int mslot = (qv < 4 ? 0 : 6) + 2 * ((qv & 2) ? b2 : b1) + (qv & 1);
+
+    for (int c0 = 0; c0 < nvp; c0 += kF32Cols) {
+        float sr[4][2][4], si[4][2][4];  // [angle][column][q]
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sr[j][c][q] = si[j][c][q] = 0.f;
+        for (int s0 = 0; s0 < un; s0 += kF32Rows) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < kF32Rows * 4 * 32; i += kF32Threads) {
+                const int row = i >> 5, l = i & 31;  // row = us * 4 + q
+                Xs[i] = X[(long long)((u0 + s0) * 4 + row) * nvq + c0 / 2 + l];
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int us = 0; us < kF32Rows; ++us) {
+                const float4 *pw = reinterpret_cast<const float4 *>(At + (s0 + us) * kF32Angles + 4 * wg);
+                const float4 pa = pw[0], pb = pw[1];
+                const float2 p[4] = {make_float2(pa.x, pa.y), make_float2(pa.z, pa.w),
+                                     make_float2(pb.x, pb.y), make_float2(pb.z, pb.w)};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 x = Xs[(us * 4 + q) * 32 + lane];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        cmac(sr[j][0][q], si[j][0][q], p[j], x.x, x.y);
+                        cmac(sr[j][1][q], si[j][1][q], p[j], x.z, x.w);
+                    }
+                }
+            }
+        }
+        // column factor t_v t_w; J_b1 = -H_b2, J_b2 = H_b1, M_b1 = E_b2, M_b2 = -E_b1
+        // (times the normal's sign, applied in FP64 below)
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long ang = ang0 + 4 * wg + j;
+            const float2 tw = a.tab32[(long long)ew * a.n_ang_pad + ang];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[8 * j + q] = 0.f;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int v = c0 + 2 * lane + c;
+                const float2 tv = v < nv ? a.tab32[(long long)(ev + v) * a.n_ang_pad + ang]
+                                         : make_float2(0.f, 0.f);
+                const float cr = tv.x * tw.x - tv.y * tw.y, ci = tv.x * tw.y + tv.y * tw.x;
+                const float sg[4] = {1.f, -1.f, -1.f, 1.f};   // sign of q in its output
+                const int oq[4] = {2, 0, 6, 4};               // H_b1 -> J_b2, H_b2 -> J_b1, E_b1 -> M_b2, E_b2 -> M_b1
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float xr = sg[q] * sr[j][c][q], xi = sg[q] * si[j][c][q];
+                    o[8 * j + oq[q]] = fmaf(cr, xr, fmaf(-ci, xi, o[8 * j + oq[q]]));
+                    o[8 * j + oq[q] + 1] = fmaf(cr, xi, fmaf(ci, xr, o[8 * j + oq[q] + 1]));
+                }
+            }
+        }
+        rs_stage<16>(o, lane);
+        rs_stage<8>(o, lane);
+        rs_stage<4>(o, lane);
+        rs_stage<2>(o, lane);
+        rs_stage<1>(o, lane);
+        acc[(4 * wg + jv) * 12 + mslot] += sgn * (double)o[0];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kF32Angles * 12; i += kF32Threads) {
+        const int j = i / 12, m = i % 12;
+        if (ang0 + j < a.n_ang) a.partial[((long long)(ang0 + j) * a.chunks + ch) * 12 + m] = acc[i];
+    }
+}
+
 }  // namespace
 
 #define LBEM_FF_TABLES(MODE)                                                                 \
@@ -567,8 +769,81 @@ inline int grid_for(long long n, int threads)
         far_field_columns<MODE><<<g1, kFFThreads, smem, s>>>(a);                             \
     } while (0)
 
+static size_t ff32_smem(int uc)
+{
+    return (size_t)uc * kF32Angles * sizeof(float2) + (size_t)kF32Rows * 4 * 32 * sizeof(float4) +
+           (size_t)kF32Angles * 12 * sizeof(double);
+}
+
+// The 3D projection through far_field_f32: phase tables, packed faces, the
+// contraction and the FP64 finalisation.  The chunk height uc (a multiple of
+// 16 rows) minimises waves x (uc + 8): fewer, taller chunks waste less per
+// block but quantise the grid into more partial waves.
+static cudaError_t launch_far_field_f32(FarFieldArgs a, cudaStream_t s, int *launches)
+{
+    if (a.n_ang <= 0) return cudaSuccess;
+    long long off = 0;
+    for (int f = 0; f < a.g.nfaces; ++f) {
+        a.nup[f] = (a.g.nu[f] + kF32Rows - 1) / kF32Rows * kF32Rows;
+        a.nvp[f] = (a.g.nv[f] + kF32Cols - 1) / kF32Cols * kF32Cols;
+        a.off32[f] = off;
+        off += (long long)a.nup[f] * 4 * a.nvp[f];
+    }
+    a.off32[a.g.nfaces] = off;
+    a.n_ang_pad = (a.n_ang + kF32Angles - 1) / kF32Angles * kF32Angles;
+    const int ne = (a.g.hi[0] - a.g.lo[0] + 1) + (a.g.hi[1] - a.g.lo[1] + 1) + (a.g.hi[2] - a.g.lo[2] + 1);
+    if (off > a.x32_cap || (long long)ne * a.n_ang_pad > a.tab32_cap) return cudaErrorInvalidValue;
+    // resident blocks per SM for each chunk height (shared memory grows with uc)
+    constexpr int kMaxUc = 512;
+    static int sms = 0, per_uc[kMaxUc / kF32Rows + 1];
+    cudaError_t e = cudaSuccess;
+    if (sms == 0) {
+        int dev = 0, n = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(far_field_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ff32_smem(kMaxUc));
+        for (int uc = kF32Rows; e == cudaSuccess && uc <= kMaxUc; uc += kF32Rows)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_uc[uc / kF32Rows], far_field_f32,
+                                                               kF32Threads, ff32_smem(uc));
+        if (e != cudaSuccess) return e;
+        sms = n;
+    }
+    const int tiles = a.n_ang_pad / kF32Angles;
+    int best_uc = 0;
+    double best = 0.0;
+    for (int uc = kF32Rows; uc <= kMaxUc; uc += kF32Rows) {
+        int chunks = 0;
+        for (int f = 0; f < a.g.nfaces; ++f) chunks += (a.nup[f] + uc - 1) / uc;
+        const int per = per_uc[uc / kF32Rows];
+        if (chunks > kMaxChunks || per < 1) continue;
+        const long long blocks = (long long)tiles * chunks;
+        const long long waves = (blocks + (long long)per * sms - 1) / ((long long)per * sms);
+        const double t = (double)waves * (uc + 8);
+        if (best_uc == 0 || t < best) {
+            best = t;
+            best_uc = uc;
+        }
+    }
+    if (best_uc == 0) return cudaErrorInvalidValue;
+    a.uc = best_uc;
+    a.chunk_start[0] = 0;
+    for (int f = 0; f < a.g.nfaces; ++f) a.chunk_start[f + 1] = a.chunk_start[f] + (a.nup[f] + a.uc - 1) / a.uc;
+    a.chunks = a.chunk_start[a.g.nfaces];
+    const size_t sm = ff32_smem(a.uc);
+    const long long nt = (long long)ne * a.n_ang_pad;
+    ff32_tables<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(a);
+    ff32_pack<<<(unsigned)((off + 255) / 256), 256, 0, s>>>(a);
+    far_field_f32<<<dim3(tiles, a.chunks), kF32Threads, sm, s>>>(a);
+    far_field_finalize<<<(a.n_ang + 127) / 128, 128, 0, s>>>(a);
+    if (launches) *launches += 4;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_far_field(const FarFieldArgs &a, cudaStream_t s, int *launches)
 {
+    if (a.mode == 2 && a.x32 != nullptr) return launch_far_field_f32(a, s, launches);
     dim3 g1(a.chunks, a.n_ang);
     const int entries = (a.g.hi[0] - a.g.lo[0] + 1) + (a.g.hi[1] - a.g.lo[1] + 1) + (a.g.hi[2] - a.g.lo[2] + 1);
     const bool tables = entries <= kFFTableMax;
