@@ -8,7 +8,9 @@ x-polarised plane wave along +z, 16-cell absorbing layer).  One bench step is
 one pass of the whole hot path: one DFT window of T = 3 lambda = 90 lattice
 updates (pull streaming with the Eq. 4 boundary, TF/SF source, moments,
 running FP64 DFT on the NTFF box, collision, absorbing layer) followed by the
-FP64 near-to-far-field projection to |S(theta, phi)|^2 at 181 x 3 angles.
+near-to-far-field projection to |S(theta, phi)|^2 at 181 x 3 angles (an FP32
+contraction with FP64 sums above chunks of face rows; the FP64-throughout
+projection is timed beside it, outside the timed region).
 The default 3 warm-up + 27 timed steps run the 30 periods of the workload, so
 the last step's |S|^2 is the steady-state result compared with Mie.
 
@@ -264,6 +266,19 @@ def run_gpu(args, rank, world, local_rank):
             out["e2e_s_per_step"] = t_e2e
             out["h2d_bytes"] = int(prob.eps.nbytes + theta.nbytes + phi.nbytes)
             out["d2h_bytes"] = int(theta.size * 8)
+            # the projection's two precisions on this window's DFT (outside the timed region)
+            ff, vals = {}, {}
+            for prec in ("mixed", "fp64"):
+                lbem.lbem_set_far_field_precision(h, prec)
+                lbem.lbem_far_field(h, theta, phi)
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    vals[prec] = lbem.lbem_far_field(h, theta, phi)
+                ff[prec + "_ms_per_call"] = round((time.perf_counter() - t0) / 3 * 1e3, 3)
+            lbem.lbem_set_far_field_precision(h, "mixed")
+            d = vals["mixed"] - vals["fp64"]
+            ff["rel_l2_mixed_vs_fp64"] = float(np.linalg.norm(d) / np.linalg.norm(vals["fp64"]))
+            out["far_field"] = ff
         solver.close()
         del solver
         torch.cuda.empty_cache()
@@ -332,6 +347,9 @@ def run_gpu(args, rank, world, local_rank):
         "mie": {"nrms_phi_0_45_90": [round(v, 5) for v in main["mie_nrms"]],
                 "periods_run": main["periods"], "incident_amplitude": round(main["incident"], 6)},
         "storage_modes": storage_modes,
+        "far_field": dict(main["far_field"], angles=int(theta.size),
+                          default="mixed: FP32 products, FP32 sums over <= 32 face rows and a 64-column "
+                                  "tile, FP64 sums above"),
     }
     if probe_2d:
         line["bandwidth_probe_2d"] = probe_2d

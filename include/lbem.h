@@ -203,6 +203,15 @@ int32_t lbem_set_permeability(lbem_handle h, const float *mu_r, int32_t mu_on_de
 int32_t lbem_far_field(lbem_handle h, const double *theta_host, const double *phi_host,
                        int32_t n, double *s2_host, double *amp_host);
 
+/* Precision of the 3D projection in lbem_far_field (2D is always FP64).
+ * LBEM_FAR_FIELD_MIXED (the default): the FP32 contraction described above.
+ * LBEM_FAR_FIELD_FP64: FP64 products and sums throughout, ~30x slower on
+ * GB300 (its FP64 pipe runs at 1/64 of the FP32 rate).  Anything else:
+ * LBEM_ERR_ARG with the setting unchanged. */
+#define LBEM_FAR_FIELD_MIXED 0
+#define LBEM_FAR_FIELD_FP64 1
+int32_t lbem_set_far_field_precision(lbem_handle h, int32_t precision);
+
 /* |E_I| as used by lbem_far_field. */
 int32_t lbem_incident_amplitude(lbem_handle h, double *out_host);
 

@@ -45,6 +45,7 @@ struct lbem_ctx {
     float2 *x32 = nullptr;      // 3D far field in FP32: packed faces, then phase tables
     float2 *tab32 = nullptr;
     size_t x32_cap = 0, tab32_cap = 0;
+    bool ff_fp64 = false;       // LBEM_FAR_FIELD_FP64: 3D projection by the FP64 kernels
     float *stage = nullptr;     // one FP32 plane of ncell values
     int *flag = nullptr;
     // time and source
@@ -1082,6 +1083,7 @@ static int far_field_chunks(const FaceGeom &g)
 // The 3D projection runs as an FP32 contraction in the workspace's ff32 region.
 static void set_far_field_f32(lbem_ctx *h, FarFieldArgs &a)
 {
+    if (h->ff_fp64) return;  // x32 stays NULL: the FP64 kernels
     a.x32 = h->x32;
     a.tab32 = h->tab32;
     a.x32_cap = (long long)h->x32_cap;
@@ -1146,6 +1148,15 @@ int32_t lbem_far_field(lbem_handle h, const double *theta, const double *phi, in
                                   cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
+    return LBEM_OK;
+}
+
+int32_t lbem_set_far_field_precision(lbem_handle h, int32_t precision)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (precision != LBEM_FAR_FIELD_MIXED && precision != LBEM_FAR_FIELD_FP64)
+        return fail(h, LBEM_ERR_ARG, "precision must be LBEM_FAR_FIELD_MIXED (0) or LBEM_FAR_FIELD_FP64 (1)");
+    h->ff_fp64 = precision == LBEM_FAR_FIELD_FP64;
     return LBEM_OK;
 }
 

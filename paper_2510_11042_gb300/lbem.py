@@ -77,6 +77,7 @@ _SIGS = {
     "lbem_get_time": (_I32, [_P, ctypes.POINTER(_I64)]),
     "lbem_far_field": (_I32, [_P, _P, _P, _I32, _P, _P]),
     "lbem_incident_amplitude": (_I32, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "lbem_set_far_field_precision": (_I32, [_P, _I32]),
     "lbem_get_populations": (_I32, [_P, _P, _I32]),
     "lbem_set_populations": (_I32, [_P, _P, _I32]),
     "lbem_fields": (_I32, [_P, _P, _P, _I32]),
@@ -232,6 +233,15 @@ def lbem_far_field(h, theta, phi=None, with_amplitudes=False):
                                 None if phi_a is None else phi_a.ctypes.data, n, s2.ctypes.data,
                                 None if amp is None else amp.ctypes.data), h)
     return (s2, amp) if with_amplitudes else s2
+
+
+LBEM_FAR_FIELD_MIXED = 0
+LBEM_FAR_FIELD_FP64 = 1
+FAR_FIELD_PRECISION = {"mixed": LBEM_FAR_FIELD_MIXED, "fp64": LBEM_FAR_FIELD_FP64}
+
+
+def lbem_set_far_field_precision(h, precision):
+    _check(lib().lbem_set_far_field_precision(h, int(FAR_FIELD_PRECISION.get(precision, precision))), h)
 
 
 def lbem_incident_amplitude(h) -> float:
@@ -537,6 +547,10 @@ class Solver:
 
     def far_field(self, theta, phi=None, with_amplitudes=False):
         return lbem_far_field(self.h, theta, phi, with_amplitudes)
+
+    def set_far_field_precision(self, precision):
+        """"mixed" (FP32 contraction, FP64 sums above row chunks; default) or "fp64"."""
+        lbem_set_far_field_precision(self.h, precision)
 
     def incident_amplitude(self):
         return lbem_incident_amplitude(self.h)

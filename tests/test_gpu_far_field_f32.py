@@ -75,3 +75,27 @@ def test_far_field_f32_against_fp64_kernels(sphere_run, capsys):
         print(f"\n[far field FP32 vs FP64 kernels] rel-L2 {err:.2e}, worst angle {worst:.2e}")
     assert err <= TOL_F64
     assert worst <= 10 * TOL_F64
+
+
+def test_far_field_fp64_precision_switch(sphere_run):
+    """LBEM_FAR_FIELD_FP64 routes the 3D projection through the FP64 kernels
+    (the no-alloc path's arithmetic); MIXED returns to the FP32 contraction."""
+    p, s, r = sphere_run
+    from oracle import ntff
+    from paper_2510_11042_gb300 import lbem
+    th, ph = _angles(200, 7)
+    mixed = s.far_field(th, ph)
+    s.set_far_field_precision("fp64")
+    try:
+        f64 = s.far_field(th, ph)
+    finally:
+        s.set_far_field_precision("mixed")
+    assert np.array_equal(s.far_field(th, ph), mixed)
+    assert not np.array_equal(f64, mixed)
+    k = 2 * math.pi / p.wave.wavelength
+    exp = ntff.far_field(r.phasors(), p.wave.ntff_lo, p.wave.ntff_hi, k, p.wave.center,
+                         r.incident_amplitude(), "3d", th, ph)
+    assert rel_l2(f64, exp) <= TOL
+    assert rel_l2(mixed, f64) <= TOL_F64
+    with pytest.raises(lbem.LbemError):
+        s.set_far_field_precision(2)
