@@ -46,6 +46,12 @@ struct lbem_ctx {
     float2 *tab32 = nullptr;
     size_t x32_cap = 0, tab32_cap = 0;
     bool ff_fp64 = false;       // LBEM_FAR_FIELD_FP64: 3D projection by the FP64 kernels
+    // deferred DFT of the NTFF box's x faces (see dft_flush_x_kernel)
+    float *xstage = nullptr;    // [kXStage][NC][xs_n]
+    size_t xstage_floats = 0;
+    long long xs_n = 0;         // cells of the two x faces (0: none)
+    int xs_cnt = 0;             // staged steps not yet summed
+    double xs_sc[kXStage], xs_ss[kXStage];
     float *stage = nullptr;     // one FP32 plane of ncell values
     int *flag = nullptr;
     // time and source
@@ -115,6 +121,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t f0, f1, inv_eps, inv_mu, pw_tab, line0, line1, line2, dft, line_dft, scratch, ff32, stage, flag, total;
     size_t x32_cap, tab32_cap;  // float2 capacities of the 3D FP32 far field (0 in 2D)
+    size_t xstage, xstage_floats;  // staged x-face DFT fields
     int Q, nxp, n_line_max;
     long long P, ncell;
     size_t elem, dft_doubles_max, scratch_doubles;
@@ -183,6 +190,10 @@ static Layout make_layout(const lbem_grid_desc *g)
         L.tab32_cap = (size_t)(g->nx + g->ny + g->nz) * kAngleBatch;
     }
     L.ff32 = take((L.x32_cap + L.tab32_cap) * 8);
+    // kXStage steps of the x faces' fields; the faces of any NTFF box are
+    // bounded by the grid's two x faces (ny * nz cells each)
+    L.xstage_floats = g->mode == 2 ? (size_t)kXStage * NC * 2 * g->ny * g->nz : 0;
+    L.xstage = take(L.xstage_floats * 4);
     L.stage = take((size_t)L.ncell * 4);
     L.flag = take(256);
     L.total = o;
@@ -381,6 +392,8 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->line_dft = (double *)(h->ws + L.line_dft);
     h->scratch = (double *)(h->ws + L.scratch);
     h->scratch_doubles = L.scratch_doubles;
+    h->xstage = (float *)(h->ws + L.xstage);
+    h->xstage_floats = L.xstage_floats;
     h->x32_cap = L.x32_cap;
     h->tab32_cap = L.tab32_cap;
     h->x32 = L.x32_cap ? (float2 *)(h->ws + L.ff32) : nullptr;
@@ -468,6 +481,10 @@ static void build_faces(lbem_ctx *h)
     }
     F.cell_start[F.nfaces] = cells;
     h->dft_doubles = (size_t)off;
+    // faces 0 and 1 are the x faces when the grid has an x extent (staged in 3D only)
+    h->xs_n = (h->g.mode == 2 && F.nfaces >= 2 && F.axis[0] == 0) ? 2LL * F.nu[0] * F.nv[0] : 0;
+    if ((size_t)h->xs_n * h->NC * kXStage > h->xstage_floats) h->xs_n = 0;  // cannot happen: bounded by the grid
+    h->xs_cnt = 0;
 }
 
 static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w);
@@ -637,6 +654,7 @@ static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w)
         build_faces(h);
     } else {
         h->faces.nfaces = 0;
+        h->xs_n = 0;
         h->faces.cell_start[0] = 0;
         h->dft_doubles = 0;
     }
@@ -660,6 +678,31 @@ int32_t lbem_set_dft_window(lbem_handle h, int64_t t_start, int32_t n_periods)
     h->dft_periods = n_periods;
     CK(h, cudaMemsetAsync(h->dft, 0, h->dft_doubles * 8, h->stream));
     CK(h, cudaMemsetAsync(h->line_dft, 0, (size_t)h->n_line_max * 6 * 8, h->stream));
+    return LBEM_OK;
+}
+
+// Sum the staged x-face DFT fields into the accumulators (dft_flush_x_kernel).
+static int flush_x_stage(lbem_ctx *h)
+{
+    if (h->xs_cnt == 0) return LBEM_OK;
+    DftFlushArgs f;
+    std::memset(&f, 0, sizeof f);
+    f.stage = h->xstage;
+    f.n = h->xs_n;
+    f.plane = (long long)h->faces.nu[0] * h->faces.nv[0];
+    f.nc = h->NC;
+    f.cnt = h->xs_cnt;
+    f.dft = h->dft;
+    f.face_off[0] = h->faces.off[0];
+    f.face_off[1] = h->faces.off[1];
+    for (int s = 0; s < h->xs_cnt; ++s) {
+        f.sc[s] = h->xs_sc[s];
+        f.ss[s] = h->xs_ss[s];
+    }
+    h->xs_cnt = 0;
+    cudaError_t e = launch_dft_flush_x(f, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "x-face DFT flush launch");
+    h->launches += 1;
     return LBEM_OK;
 }
 
@@ -699,7 +742,16 @@ int32_t lbem_step(lbem_handle h, int64_t n)
                 a.dft_s = std::sin(ph);
                 a.dft_scale = 2.0 / ((double)h->dft_periods * h->T);  // line (FP32, unscaled)
                 a.dft_scale_cells = a.dft_scale * h->scale;            // lattice (storage units)
+                a.dft_sc = a.dft_scale_cells * a.dft_c;
+                a.dft_ss = a.dft_scale_cells * a.dft_s;
             }
+        }
+        a.xstage = nullptr;
+        if (a.dft_on && h->xs_n > 0) {
+            a.xstage = h->xstage + (size_t)h->xs_cnt * h->NC * h->xs_n;
+            a.xs_n = h->xs_n;
+            h->xs_sc[h->xs_cnt] = a.dft_sc;
+            h->xs_ss[h->xs_cnt] = a.dft_ss;
         }
         cudaError_t e = h->analytic ? launch_step_analytic(h->g.mode, h->g.storage, a, h->stream)
                         : h->mu_on  ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
@@ -708,8 +760,12 @@ int32_t lbem_step(lbem_handle h, int64_t n)
         h->launches += 1;
         h->cur ^= 1;
         h->t = t;
+        if (a.xstage && ++h->xs_cnt == kXStage) {
+            const int rc = flush_x_stage(h);
+            if (rc != LBEM_OK) return rc;
+        }
     }
-    return LBEM_OK;
+    return flush_x_stage(h);  // every call leaves the DFT complete
 }
 
 // ------------------------------------------------------------ batched runs

@@ -211,6 +211,9 @@ struct StepArgs {
     double dft_c, dft_s;
     double dft_scale;          // 2/(P T): incident line (FP32 units)
     double dft_scale_cells;    // 2/(P T) times the storage scale: lattice cells
+    double dft_sc, dft_ss;     // dft_scale_cells times cos, sin of the step's phase
+    float *xstage;             // 3D, non-NULL: x-face fields go here ([NC][xs_n]) for dft_flush_x
+    long long xs_n;            // cells of the two x faces
     int nt_lo[3], nt_hi[3];
     double *dft;
     long long face_off[kMaxFaces];
@@ -295,6 +298,20 @@ struct FaceGeom {
     long long cell_start[kMaxFaces + 1];  // prefix sum of nu*nv
     int lo[3], hi[3];
 };
+
+// Deferred DFT of the two x faces of the NTFF box: kXStage steps of staged
+// fields [step][NC][xs_n] and their phase coefficients.
+constexpr int kXStage = 16;
+struct DftFlushArgs {
+    const float *stage;
+    long long n;               // cells of the two x faces (side-major, then [nu][nv])
+    long long plane;           // nu * nv of one x face
+    int nc, cnt;
+    double *dft;
+    long long face_off[2];
+    double sc[kXStage], ss[kXStage];
+};
+cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s);
 
 struct FarFieldArgs {
     const double *dft;

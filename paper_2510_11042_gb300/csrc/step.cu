@@ -314,13 +314,26 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
                 const int ua = ax == 2 ? 1 : 2, va = ax == 0 ? 1 : 0;
                 const int iu = g[ua] - a.nt_lo[ua], iv = g[va] - a.nt_lo[va];
                 const int nu = a.face_nu[face], nv = a.face_nv[face];
+                if constexpr (MODE == 2) {
+                    if (ax == 0 && a.xstage) {
+                        // x faces hold two cells per row, one thread in a warp:
+                        // their read-modify-write would hold the warp for a DRAM
+                        // round trip and a lone FP64 pass, so they store the
+                        // fields and dft_flush_x sums them in full warps (3D
+                        // only: in 2D the branch cost more than it saved)
+                        const long long j = ((long long)side * nu + iu) * nv + iv;
+#pragma unroll
+                        for (int k = 0; k < PL::NC; ++k) a.xstage[(long long)k * a.xs_n + j] = vals[k];
+                        continue;
+                    }
+                }
                 double *base = a.dft + a.face_off[face] + (long long)iu * nv + iv;
                 const long long plane = (long long)nu * nv;
 #pragma unroll
                 for (int k = 0; k < PL::NC; ++k) {
-                    const double v = a.dft_scale_cells * (double)vals[k];
-                    base[(2 * k + 0) * plane] += v * a.dft_c;
-                    base[(2 * k + 1) * plane] -= v * a.dft_s;
+                    const double v = (double)vals[k];
+                    base[(2 * k + 0) * plane] = fma(v, a.dft_sc, base[(2 * k + 0) * plane]);
+                    base[(2 * k + 1) * plane] = fma(v, -a.dft_ss, base[(2 * k + 1) * plane]);
                 }
             }
         }
@@ -659,6 +672,8 @@ __device__ void fill_step_args(StepArgs &sa, const BatchProblem &P, long long st
         sa.dft_s = sp;
         sa.dft_scale = 2.0 / ((double)P.dft_periods * P.T);
         sa.dft_scale_cells = sa.dft_scale * P.scale;
+        sa.dft_sc = sa.dft_scale_cells * cp;
+        sa.dft_ss = sa.dft_scale_cells * sp;
     }
 }
 
@@ -725,6 +740,27 @@ __global__ void line_init_kernel(const StepArgs a)
                         a.inc_axis);
 }
 
+
+// Sums cnt staged steps of x-face fields into the FP64 DFT accumulators in
+// step order, with the same fma as the direct path: one thread per (cell,
+// component), reads coalesced along the cells.
+__global__ void dft_flush_x_kernel(const DftFlushArgs a)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n * a.nc) return;
+    const long long j = i % a.n;
+    const int k = (int)(i / a.n);
+    const int side = (int)(j / a.plane);
+    double *base = a.dft + a.face_off[side] + (j - side * a.plane);
+    double re = base[(2 * k + 0) * a.plane], im = base[(2 * k + 1) * a.plane];
+    for (int s = 0; s < a.cnt; ++s) {
+        const double v = (double)a.stage[((long long)s * a.nc + k) * a.n + j];
+        re = fma(v, a.sc[s], re);
+        im = fma(v, -a.ss[s], im);
+    }
+    base[(2 * k + 0) * a.plane] = re;
+    base[(2 * k + 1) * a.plane] = im;
+}
 
 template <int MODE, class S, bool REC = false, bool MU = false, bool ANA = false>
 cudaError_t launch_cell(StepArgs a, cudaStream_t s)
@@ -802,6 +838,14 @@ int batch_max_blocks_per_sm(int mode, int storage)
     case 8: return max_blocks_t<2, __nv_bfloat16>();
     default: return 0;
     }
+}
+
+cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s)
+{
+    if (a.cnt < 1 || a.cnt > kXStage || a.n <= 0) return cudaErrorInvalidValue;
+    const long long total = a.n * a.nc;
+    dft_flush_x_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s)

@@ -324,3 +324,32 @@ def test_storage_scale_and_checkpoint_in_grouped_16bit_layout(storage):
     assert lbem.lbem_get_storage_scale(t.h) == old * 4.0
     t.step(20)
     np.testing.assert_array_equal(t.populations(), ref)
+
+
+@pytest.mark.parametrize("mode", ["ez", "3d"])
+def test_dft_same_for_any_step_split(mode):
+    """The x faces' DFT terms are staged and summed in 16-step batches and at
+    the end of every lbem_step call, in the same order and with the same fma
+    as the other faces: one call for the whole run and one call per step give
+    the same accumulators bit for bit, and they match the FP64 oracle."""
+    if mode == "ez":
+        p = W.cylinder_problem(n=72, x=3.0, wavelength=10.0, eps_in=2.25, w=6, mode="ez", periods=8)
+    else:
+        p = W.sphere_problem(n=36, x=2.0, wavelength=10.0, eps_in=2.0, w=4, periods=3,
+                             gap_ntff=2, gap_tf=2)
+    steps = p.steps
+    a = gpu_solver(p, steps=0)
+    b = gpu_solver(p, steps=0)
+    a.step(steps)
+    for _ in range(steps):
+        b.step(1)
+    da, db = a.dft(), b.dft()
+    assert np.array_equal(da, db)
+    assert np.abs(da).max() > 0
+    r = oracle_run(p)
+    from paper_2510_11042_gb300 import lbem
+    faces = lbem.dft_faces(da, mode, p.shape, p.wave.ntff_lo, p.wave.ntff_hi)
+    ref = oracle_faces(r.phasors(), mode, p.wave.ntff_lo, p.wave.ntff_hi)
+    got = np.concatenate([f["data"].ravel() for f in faces])
+    exp = np.concatenate([f.ravel() for f in ref])
+    assert rel_l2(got, exp) <= TOL
