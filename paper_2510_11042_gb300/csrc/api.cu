@@ -276,6 +276,10 @@ static void fill_common_args(lbem_ctx *h, StepArgs &a)
         a.pw_d = h->pw_d;
         a.pw_amp = (float)h->pw.amp;
         a.pw_t_ramp = (float)h->pw.t_ramp;
+        for (int c = 0; c < 3; ++c) {
+            a.pw_polf[c] = (float)h->pw.pol[c];
+            a.pw_kxpf[c] = (float)h->pw.kxp[c];
+        }
     }
     for (int k = 0; k < 3; ++k) {
         a.tf_lo[k] = h->wave.tfsf_lo[k];

@@ -201,6 +201,7 @@ struct StepArgs {
     float2 pw_wt[2];
     float pw_t[2];
     float pw_amp, pw_t_ramp;
+    float pw_polf[3], pw_kxpf[3];  // polarisation p and k x p in FP32
     int tf_lo[3], tf_hi[3];
     int inc_axis;
     const float *line_n;

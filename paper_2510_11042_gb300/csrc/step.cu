@@ -178,76 +178,118 @@ __device__ __forceinline__ void line_work(const StepArgs &a, int s)
 // sin(w tau) = Im(exp(j w t_s) prod_a exp(-j w 3 k_a (p_a - r0_a))).  All
 // factors have unit modulus, so the phase carries no growing rounding error;
 // tau (only needed during the ramp) is formed from small terms.
-__device__ __forceinline__ float pw_amp_tab(const StepArgs &a, int px, int py, int pz, int s)
+__device__ __forceinline__ float2 cmulf(float2 p, float2 q)
 {
-    const float2 fx = __ldg(a.pw_ph + px), fy = __ldg(a.pw_ph + a.nx + py),
-                 fz = __ldg(a.pw_ph + a.nx + a.ny + pz);
-    const float2 fxy = make_float2(fx.x * fy.x - fx.y * fy.y, fx.x * fy.y + fx.y * fy.x);
-    const float2 f = make_float2(fxy.x * fz.x - fxy.y * fz.y, fxy.x * fz.y + fxy.y * fz.x);
+    return make_float2(p.x * q.x - p.y * q.y, p.x * q.y + p.y * q.x);
+}
+
+// f = prod_a exp(-j w 3 k_a (p_a - r0_a)) and dsum = sum_a 3 k_a (p_a - r0_a)
+// of a cell, then the amplitude at time t_s (s = 0: t_n, 1: t_n+1).
+__device__ __forceinline__ float pw_amp_from(const StepArgs &a, float2 f, float dsum, int s)
+{
     const float2 w = a.pw_wt[s];
     const float sn = w.x * f.y + w.y * f.x;
-    const float tau = a.pw_t[s] - (__ldg(a.pw_d + px) + __ldg(a.pw_d + a.nx + py) +
-                                   __ldg(a.pw_d + a.nx + a.ny + pz));
+    const float tau = a.pw_t[s] - dsum;
     float ramp = 1.f;
     if (tau <= 0.f) ramp = 0.f;
     else if (tau < a.pw_t_ramp) ramp = 0.5f * (1.f - cospif(tau / a.pw_t_ramp));
     return a.pw_amp * ramp * sn;
 }
 
-template <int MODE>
-__device__ __forceinline__ void analytic_source(const StepArgs &a, int x, int y, int z, float inv_eps,
-                                                float inv_mu, float keep, float *src)
+// In-mode field components: EZ carries E_z, H_x, H_y; HZ E_x, E_y, H_z; 3D all.
+template <int MODE> __device__ __forceinline__ constexpr bool in_e(int c)
 {
-    using PL = Planes<MODE>;
-    constexpr int Q = PL::Q;
+    return MODE == 2 || (MODE == 0 ? c == 2 : c < 2);
+}
+template <int MODE> __device__ __forceinline__ constexpr bool in_h(int c)
+{
+    return MODE == 2 || (MODE == 0 ? c < 2 : c == 2);
+}
+
+// The analytic source of one cell, reduced to what its populations need.
+// Population q of direction i != 0 of the vacuum equilibrium of a wave of
+// amplitude u is u P(q), P = (p - c_i x k')/6 (electric) or (k' + c_i x p)/6
+// (magnetic), p the polarisation and k' = k x p; the rest populations are 0.
+// So keep * (2 f_eq(I_pulled) - I_pulled) - I(r, n+1) is, per population,
+// keep * 2 f_eq(q) - b_i P(q) with b_i = keep amp_i + an, and the moments of
+// I_pulled are D = (A p - V x k')/6, B = (A k' + V x p)/6 with A = sum amp_i,
+// V = sum amp_i c_i.  Everything is prescaled by keep / scale (b by 1 / scale).
+template <int MODE> struct AnaTerms {
+    float b[7];
+    float e3[3], h3[3];   // E/3, H/3 of the pulled incident moments
+    float d0[3], b0[3];   // 2 (D - E), 2 (B - H): the rest populations
+};
+
+template <int MODE>
+__device__ __forceinline__ void analytic_prepare(const StepArgs &a, int x, int y, int z, float inv_eps,
+                                                 float inv_mu, float keep, AnaTerms<MODE> &t)
+{
     constexpr float sixth = 1.0f / 6.0f;
-    const float pol[3] = {(float)a.pw.pol[0], (float)a.pw.pol[1], (float)a.pw.pol[2]};
-    const float kxp[3] = {(float)a.pw.kxp[0], (float)a.pw.kxp[1], (float)a.pw.kxp[2]};
+    // per-axis factors at the clamped coordinates p-1, p, p+1 of the cell: the
+    // seven pulled cells differ from the cell in one coordinate, so their
+    // phase products share the pair products of the other two axes
+    float2 fa[3][3];
+    float da[3][3];
+    {
+        const int n3[3] = {a.nx, a.ny, a.nz}, p3[3] = {x, y, z};
+        int base = 0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int pk = min(max(p3[ax] - 1 + k, 0), n3[ax] - 1);
+                fa[ax][k] = __ldg(a.pw_ph + base + pk);
+                da[ax][k] = __ldg(a.pw_d + base + pk);
+            }
+            base += n3[ax];
+        }
+    }
+    const float2 gxy = cmulf(fa[0][1], fa[1][1]), gxz = cmulf(fa[0][1], fa[2][1]),
+                 gyz = cmulf(fa[1][1], fa[2][1]);
+    const float2 fc = cmulf(gxy, fa[2][1]);
+    const float dc = da[0][1] + da[1][1] + da[2][1];
     float amp[7];
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
-        const int d = dir_axis(i), sg = dir_sign(i);
-        const int px = min(max(x - (d == 0 ? sg : 0), 0), a.nx - 1);
-        const int py = min(max(y - (d == 1 ? sg : 0), 0), a.ny - 1);
-        const int pz = min(max(z - (d == 2 ? sg : 0), 0), a.nz - 1);
-        amp[i] = pw_amp_tab(a, px, py, pz, 0);
+    for (int i = 1; i < 7; ++i) {
+        const int d = dir_axis(i), k = 1 - dir_sign(i);  // the pull reads p - c_i
+        const float2 f = d == 0 ? cmulf(fa[0][k], gyz) : (d == 1 ? cmulf(fa[1][k], gxz) : cmulf(fa[2][k], gxy));
+        const float dsum = da[0][d == 0 ? k : 1] + da[1][d == 1 ? k : 1] + da[2][d == 2 ? k : 1];
+        amp[i] = pw_amp_from(a, f, dsum, 0);
     }
-    float D[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int i = PL::dir(q), c = PL::comp(q);
-        const float E[3] = {amp[i] * pol[0], amp[i] * pol[1], amp[i] * pol[2]};
-        const float H[3] = {amp[i] * kxp[0], amp[i] * kxp[1], amp[i] * kxp[2]};
-        float v = 0.f;
-        if (i != 0) v = PL::fam(q) == 0 ? (E[c] - cross_c(i, H, c)) * sixth : (H[c] + cross_c(i, E, c)) * sixth;
-        src[q] = v;
-        if (PL::fam(q) == 0) D[c] += v;
-        else B[c] += v;
-    }
-    float E[3], H[3], E3[3], H3[3];
+    const float an = pw_amp_from(a, fc, dc, 1);
+    const float *pol = a.pw_polf, *kxp = a.pw_kxpf;
+    const float A = ((amp[1] + amp[2]) + (amp[3] + amp[4])) + (amp[5] + amp[6]);
+    const float V[3] = {amp[1] - amp[2], amp[3] - amp[4], amp[5] - amp[6]};
+    const float s = keep * a.inv_scale;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        E[c] = D[c] * inv_eps;
-        H[c] = B[c] * inv_mu;
-        E3[c] = third(E[c]);
-        H3[c] = third(H[c]);
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        const float D = in_e<MODE>(c) ? (A * pol[c] - (V[c1] * kxp[c2] - V[c2] * kxp[c1])) * sixth : 0.f;
+        const float B = in_h<MODE>(c) ? (A * kxp[c] + (V[c1] * pol[c2] - V[c2] * pol[c1])) * sixth : 0.f;
+        const float E = D * inv_eps, H = B * inv_mu;
+        t.e3[c] = s * third(E);
+        t.h3[c] = s * third(H);
+        t.d0[c] = s * (2.f * (D - E));
+        t.b0[c] = s * (2.f * (B - H));
     }
-    const float an = pw_amp_tab(a, x, y, z, 1);
-    const float En[3] = {an * pol[0], an * pol[1], an * pol[2]};
-    const float Hn[3] = {an * kxp[0], an * kxp[1], an * kxp[2]};
+    t.b[0] = 0.f;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int i = PL::dir(q), c = PL::comp(q);
-        float eq2, In = 0.f;
-        if (PL::fam(q) == 0) {
-            eq2 = (i == 0) ? 2.f * (D[c] - E[c]) : E3[c] - cross_c(i, H3, c);
-            if (i != 0) In = (En[c] - cross_c(i, Hn, c)) * sixth;
-        } else {
-            eq2 = (i == 0) ? 2.f * (B[c] - H[c]) : H3[c] + cross_c(i, E3, c);
-            if (i != 0) In = (Hn[c] + cross_c(i, En, c)) * sixth;
-        }
-        src[q] = (keep * (eq2 - src[q]) - In) * a.inv_scale;
+    for (int i = 1; i < 7; ++i) t.b[i] = (keep * amp[i] + an) * a.inv_scale;
+}
+
+template <int MODE>
+__device__ __forceinline__ float analytic_term(const StepArgs &a, const AnaTerms<MODE> &t, int q)
+{
+    using PL = Planes<MODE>;
+    constexpr float sixth = 1.0f / 6.0f;
+    const int i = PL::dir(q), c = PL::comp(q);
+    const float *pol = a.pw_polf, *kxp = a.pw_kxpf;
+    if (PL::fam(q) == 0) {
+        if (i == 0) return t.d0[c];
+        return (t.e3[c] - cross_c(i, t.h3, c)) - t.b[i] * ((pol[c] - cross_c(i, kxp, c)) * sixth);
     }
+    if (i == 0) return t.b0[c];
+    return (t.h3[c] + cross_c(i, t.e3, c)) - t.b[i] * ((kxp[c] + cross_c(i, pol, c)) * sixth);
 }
 
 // Accessor of one cell's pulled populations held in registers.
@@ -367,8 +409,10 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
         }
         return;
     }
-    float asrc[ANA ? Q : 1];
-    if (ANA && ana) analytic_source<MODE>(a, x, y, z, inv_eps, inv_mu, keep, asrc);
+    AnaTerms<MODE> at;
+    if constexpr (ANA) {
+        if (ana) analytic_prepare<MODE>(a, x, y, z, inv_eps, inv_mu, keep, at);
+    }
     float dE[3] = {0.f, 0.f, 0.f}, dE3[3] = {0.f, 0.f, 0.f};
     float dH[3] = {0.f, 0.f, 0.f}, dH3[3] = {0.f, 0.f, 0.f};
     if (source) {
@@ -409,7 +453,7 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
         }
         float v = (eq2 - f.get(q) + src) * keep;
         if constexpr (ANA) {
-            if (ana) v += asrc[q];
+            if (ana) v += analytic_term<MODE>(a, at, q);
         }
         f.set(q, v);
     }
@@ -574,13 +618,15 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
 // several rows cut the per-block start-up cost of short 128-cell rows; grids
 // of under one wave of such blocks (152 SMs x 7) take one row per block
 // instead (ONE), so that every SM gets work.  72 registers (7 blocks of 128
-// threads per SM) hold a cell without spilling.  These were chosen by timing
+// threads per SM) hold a cell without spilling; the 3D kernel with the
+// closed-form source (ANA) also holds the source terms and takes 96 (5 blocks:
+// 2.83 ms at 384^3, against 3.98 ms spilling at 7).  These were chosen by timing
 // the 384^3 sphere and 256^2 to 4096^2 EZ grids on GB300.
 template <class S> __host__ __device__ constexpr int rows_of() { return sizeof(S) == 4 ? 2 : 4; }
 constexpr long long kWaveBlocks = 152LL * 7;
 
 template <int MODE, class S, int BX, bool REC = false, bool MU = false, bool ANA = false, bool ONE = false>
-__global__ void __launch_bounds__(BX, 7) step_kernel_cell(const StepArgs a)
+__global__ void __launch_bounds__(BX, (ANA && MODE == 2) ? 5 : 7) step_kernel_cell(const StepArgs a)
 {
     constexpr int R = ONE ? 1 : rows_of<S>();
     const int b = blockIdx.x;
