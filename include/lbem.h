@@ -273,7 +273,10 @@ int32_t lbem_get_storage_scale(lbem_handle h, float *scale_out);
  * launch each (such a grid fills much of the GPU by itself, and the
  * persistent kernel's grid barrier would only add to its step) while the rest
  * share the persistent launch, and keeps one when it is faster
- * (lbem_batch_config's split = 1).  autotune = 0 runs everything persistent
+ * (lbem_batch_config's split = 1).  In a split schedule the large grids run
+ * on four internal lane streams (problem j on lane j mod 4, in turns of 64
+ * steps) forked from and joined back into cuda_stream, so that they overlap;
+ * the persistent launch follows them.  autotune = 0 runs everything persistent
  * at the largest resident shape; autotune = 2 forces the split schedule at
  * 2^19 cells without timing.
  * The handles' own streams are synchronised first; the batch runs on

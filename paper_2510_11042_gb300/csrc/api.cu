@@ -787,6 +787,8 @@ struct lbem_batch_ctx {
     long long split_cells = 0;       // size from which a grid counts as large
     double best_ms = 0.0;
     int64_t launches = 0;
+    cudaStream_t lanes[4] = {};      // streams of the large grids in a split schedule
+    cudaEvent_t lane_ev[5] = {};     // lane joins and the fork from the batch stream
     char err[512];
 };
 
@@ -851,6 +853,18 @@ extern "C" int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, 
         }
         b->owns_ws = true;
     }
+    for (int l = 0; l < 4; ++l)
+        if (cudaStreamCreateWithFlags(&b->lanes[l], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            lbem_batch_destroy(b);
+            return bfail(nullptr, LBEM_ERR_CUDA, "stream creation failed");
+        }
+    for (int l = 0; l < 5; ++l)
+        if (cudaEventCreateWithFlags(&b->lane_ev[l], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            lbem_batch_destroy(b);
+            return bfail(nullptr, LBEM_ERR_CUDA, "event creation failed");
+        }
     b->table = (BatchProblem *)b->ws;
     b->bar = (unsigned *)(b->ws + align256((size_t)count * sizeof(BatchProblem)));
     b->status = (int *)(b->bar + 2);
@@ -951,25 +965,54 @@ static int batch_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t ch
 // pay off below it.
 constexpr long long kSplitCells = 1LL << 19;
 
-// The large grids advance by plain step launches on the batch stream, the
-// others in one persistent launch; ev0 / ev1 (optional) bracket both.
+// Steps per turn when the large grids take turns on the lanes.
+constexpr int64_t kLaneSteps = 64;
+
+// The large grids advance by plain step launches, the others in one
+// persistent launch after them; ev0 / ev1 (optional) bracket both.  The large
+// grids run on up to four lane streams, problem j always on lane j mod 4 (so
+// its own steps stay in order), issued in turns of kLaneSteps steps: grids too
+// small to fill the GPU alone, and the tail of every launch, then overlap with
+// the other lanes' work.  The lanes fork from and join back into the batch
+// stream through events.
 static int split_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t chunk, int bps, int rpi,
                        const std::vector<int> &small, const std::vector<int> &big, cudaEvent_t ev0,
                        cudaEvent_t ev1)
 {
     if (ev0) cudaEventRecord(ev0, b->stream);
-    for (int i : big) {
-        lbem_ctx *h = b->hs[i];
-        const int64_t k = std::min<int64_t>(left[i], chunk);
-        cudaStream_t own = h->stream;
-        h->stream = b->stream;
-        const int64_t l0 = h->launches;
-        const int rc = lbem_step(h, k);
-        h->stream = own;
-        if (rc != LBEM_OK) return bfail(b, rc, "step of problem %d: %s", i, h->err);
-        b->launches += h->launches - l0;
-        left[i] -= k;
+    const int L = std::min<int>(4, (int)big.size());
+    if (L > 0) {
+        if (cudaEventRecord(b->lane_ev[4], b->stream) != cudaSuccess)
+            return bfail(b, LBEM_ERR_CUDA, "lane fork failed");
+        for (int l = 0; l < L; ++l)
+            if (cudaStreamWaitEvent(b->lanes[l], b->lane_ev[4], 0) != cudaSuccess)
+                return bfail(b, LBEM_ERR_CUDA, "lane fork failed");
     }
+    std::vector<int64_t> todo(big.size());
+    for (size_t j = 0; j < big.size(); ++j) todo[j] = std::min<int64_t>(left[big[j]], chunk);
+    for (bool more = true; more;) {
+        more = false;
+        for (size_t j = 0; j < big.size(); ++j) {
+            if (todo[j] == 0) continue;
+            const int i = big[j];
+            lbem_ctx *h = b->hs[i];
+            const int64_t k = std::min<int64_t>(todo[j], kLaneSteps);
+            cudaStream_t own = h->stream;
+            h->stream = b->lanes[j % L];
+            const int64_t l0 = h->launches;
+            const int rc = lbem_step(h, k);
+            h->stream = own;
+            if (rc != LBEM_OK) return bfail(b, rc, "step of problem %d: %s", i, h->err);
+            b->launches += h->launches - l0;
+            left[i] -= k;
+            todo[j] -= k;
+            more = more || todo[j] > 0;
+        }
+    }
+    for (int l = 0; l < L; ++l)
+        if (cudaEventRecord(b->lane_ev[l], b->lanes[l]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream, b->lane_ev[l], 0) != cudaSuccess)
+            return bfail(b, LBEM_ERR_CUDA, "lane join failed");
     if (!small.empty()) {
         const int rc = batch_chunk(b, left, chunk, bps, rpi, nullptr, nullptr, small);
         if (rc != LBEM_OK) return rc;
@@ -1115,6 +1158,13 @@ extern "C" const char *lbem_batch_last_error(lbem_batch b) { return b ? b->err :
 extern "C" void lbem_batch_destroy(lbem_batch b)
 {
     if (!b) return;
+    for (int l = 0; l < 4; ++l)
+        if (b->lanes[l]) {
+            cudaStreamSynchronize(b->lanes[l]);
+            cudaStreamDestroy(b->lanes[l]);
+        }
+    for (int l = 0; l < 5; ++l)
+        if (b->lane_ev[l]) cudaEventDestroy(b->lane_ev[l]);
     if (b->owns_ws) {
         cudaStreamSynchronize(b->stream);
         cudaFree(b->ws);
