@@ -46,11 +46,16 @@ struct lbem_ctx {
     float2 *tab32 = nullptr;
     size_t x32_cap = 0, tab32_cap = 0;
     bool ff_fp64 = false;       // LBEM_FAR_FIELD_FP64: 3D projection by the FP64 kernels
-    // deferred DFT of the NTFF box's x faces (see dft_flush_x_kernel)
+    int fuse = 2;               // steps per pass over the populations (lbem_set_step_fusion)
+    // deferred DFT of NTFF faces (see dft_flush_x_kernel)
     float *xstage = nullptr;    // [kXStage][NC][xs_n]
     size_t xstage_floats = 0;
-    long long xs_n = 0;         // cells of the two x faces (0: none)
+    long long xs_n = 0;         // cells of all faces (0: no staging)
+    unsigned xs_xmask = 0;      // the x faces (staged by single steps)
+    unsigned xs_allmask = 0;    // every face (staged by two-step passes)
     int xs_cnt = 0;             // staged steps not yet summed
+    bool xs_wide = false;       // a pending step staged faces beyond x
+    unsigned xs_masks[kXStage];
     double xs_sc[kXStage], xs_ss[kXStage];
     float *stage = nullptr;     // one FP32 plane of ncell values
     int *flag = nullptr;
@@ -121,7 +126,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t f0, f1, inv_eps, inv_mu, pw_tab, line0, line1, line2, dft, line_dft, scratch, ff32, stage, flag, total;
     size_t x32_cap, tab32_cap;  // float2 capacities of the 3D FP32 far field (0 in 2D)
-    size_t xstage, xstage_floats;  // staged x-face DFT fields
+    size_t xstage, xstage_floats;  // staged face DFT fields
     int Q, nxp, n_line_max;
     long long P, ncell;
     size_t elem, dft_doubles_max, scratch_doubles;
@@ -190,9 +195,11 @@ static Layout make_layout(const lbem_grid_desc *g)
         L.tab32_cap = (size_t)(g->nx + g->ny + g->nz) * kAngleBatch;
     }
     L.ff32 = take((L.x32_cap + L.tab32_cap) * 8);
-    // kXStage steps of the x faces' fields; the faces of any NTFF box are
-    // bounded by the grid's two x faces (ny * nz cells each)
-    L.xstage_floats = g->mode == 2 ? (size_t)kXStage * NC * 2 * g->ny * g->nz : 0;
+    // kXStage steps of face fields; the faces of any NTFF box are bounded by
+    // the grid's faces
+    L.xstage_floats = g->mode == 2 ? (size_t)kXStage * NC * 2 *
+                                         ((size_t)g->ny * g->nz + (size_t)g->nx * g->nz + (size_t)g->nx * g->ny)
+                                   : 0;
     L.xstage = take(L.xstage_floats * 4);
     L.stage = take((size_t)L.ncell * 4);
     L.flag = take(256);
@@ -485,10 +492,13 @@ static void build_faces(lbem_ctx *h)
     }
     F.cell_start[F.nfaces] = cells;
     h->dft_doubles = (size_t)off;
-    // faces 0 and 1 are the x faces when the grid has an x extent (staged in 3D only)
-    h->xs_n = (h->g.mode == 2 && F.nfaces >= 2 && F.axis[0] == 0) ? 2LL * F.nu[0] * F.nv[0] : 0;
+    // staging in 3D only; faces 0 and 1 are the x faces when the grid has an x extent
+    h->xs_n = (h->g.mode == 2 && F.nfaces > 0) ? (long long)cells : 0;
     if ((size_t)h->xs_n * h->NC * kXStage > h->xstage_floats) h->xs_n = 0;  // cannot happen: bounded by the grid
+    h->xs_xmask = (F.nfaces >= 2 && F.axis[0] == 0) ? 3u : 0u;
+    h->xs_allmask = (1u << F.nfaces) - 1u;
     h->xs_cnt = 0;
+    h->xs_wide = false;
 }
 
 static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w);
@@ -693,21 +703,83 @@ static int flush_x_stage(lbem_ctx *h)
     std::memset(&f, 0, sizeof f);
     f.stage = h->xstage;
     f.n = h->xs_n;
-    f.plane = (long long)h->faces.nu[0] * h->faces.nv[0];
     f.nc = h->NC;
     f.cnt = h->xs_cnt;
+    f.nfaces = h->faces.nfaces;
     f.dft = h->dft;
-    f.face_off[0] = h->faces.off[0];
-    f.face_off[1] = h->faces.off[1];
+    for (int k = 0; k < h->faces.nfaces; ++k) {
+        f.start[k] = h->faces.cell_start[k];
+        f.plane[k] = (long long)h->faces.nu[k] * h->faces.nv[k];
+        f.face_off[k] = h->faces.off[k];
+    }
+    f.start[h->faces.nfaces] = h->faces.cell_start[h->faces.nfaces];
     for (int s = 0; s < h->xs_cnt; ++s) {
+        f.mask[s] = h->xs_masks[s];
         f.sc[s] = h->xs_sc[s];
         f.ss[s] = h->xs_ss[s];
     }
     h->xs_cnt = 0;
+    h->xs_wide = false;
     cudaError_t e = launch_dft_flush_x(f, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "x-face DFT flush launch");
     h->launches += 1;
     return LBEM_OK;
+}
+
+// Per-step arguments of the step from time tn to tn+1 reading population
+// buffer in and writing buffer out (a holds the common arguments).
+static void step_args_at(lbem_ctx *h, StepArgs &a, int64_t tn, int in, int out)
+{
+    const int64_t t = tn + 1;  // time of the fields this step computes
+    const size_t plane_bytes = (size_t)h->P * h->elem;
+    for (int q = 0; q < h->Q; ++q) {
+        a.fin_q[q] = (const char *)h->f[in] + q * plane_bytes;
+        a.fout_q[q] = (char *)h->f[out] + q * plane_bytes;
+    }
+    a.dft_on = 0;
+    if (h->has_wave) {
+        if (!h->analytic) {
+            a.line_n = line_at(h, tn);
+            a.line_n1 = line_at(h, tn + 1);
+            a.line_out = line_at(h, tn + 2);
+            source_fields(h, tn + 2, a.src_E, a.src_H);
+        }
+        a.tn = tn;
+        if (h->analytic)
+            for (int k = 0; k < 2; ++k) {
+                const int64_t ts = tn + k;
+                const double ph = 2.0 * M_PI * (double)(ts % h->T) / (double)h->T;  // w t_s mod 2 pi
+                a.pw_wt[k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+                a.pw_t[k] = (float)ts;
+            }
+        a.dft_on = (h->faces.nfaces > 0 && h->dft_t0 >= 1 && t >= h->dft_t0 &&
+                    t < h->dft_t0 + (int64_t)h->dft_periods * h->T);
+        if (a.dft_on) {
+            const double ph = 2.0 * M_PI * (double)(t % h->T) / (double)h->T;
+            a.dft_c = std::cos(ph);
+            a.dft_s = std::sin(ph);
+            a.dft_scale = 2.0 / ((double)h->dft_periods * h->T);  // line (FP32, unscaled)
+            a.dft_scale_cells = a.dft_scale * h->scale;            // lattice (storage units)
+            a.dft_sc = a.dft_scale_cells * a.dft_c;
+            a.dft_ss = a.dft_scale_cells * a.dft_s;
+        }
+    }
+    a.xstage = nullptr;
+}
+
+// Claim the next staging slot for a step with the DFT on, staging the faces
+// in mask.
+static void stage_slot(lbem_ctx *h, StepArgs &a, unsigned mask)
+{
+    if (!a.dft_on || h->xs_n == 0 || mask == 0) return;
+    a.xstage = h->xstage + (size_t)h->xs_cnt * h->NC * h->xs_n;
+    a.xs_n = h->xs_n;
+    for (int f = 0; f < h->faces.nfaces; ++f) a.xs_start[f] = h->faces.cell_start[f];
+    h->xs_masks[h->xs_cnt] = mask;
+    h->xs_sc[h->xs_cnt] = a.dft_sc;
+    h->xs_ss[h->xs_cnt] = a.dft_ss;
+    h->xs_wide = h->xs_wide || (mask & ~h->xs_xmask) != 0;
+    ++h->xs_cnt;
 }
 
 int32_t lbem_step(lbem_handle h, int64_t n)
@@ -716,60 +788,60 @@ int32_t lbem_step(lbem_handle h, int64_t n)
     if (n < 0) return fail(h, LBEM_ERR_ARG, "n must be >= 0");
     StepArgs a;
     fill_common_args(h, a);
-    for (int64_t k = 0; k < n; ++k) {
-        const int64_t t = h->t + 1;  // time of the fields this step computes
-        const size_t plane_bytes = (size_t)h->P * h->elem;
-        for (int q = 0; q < h->Q; ++q) {
-            a.fin_q[q] = (const char *)h->f[h->cur] + q * plane_bytes;
-            a.fout_q[q] = (char *)h->f[h->cur ^ 1] + q * plane_bytes;
-        }
-        if (h->has_wave) {
-            if (!h->analytic) {
-                a.line_n = line_at(h, h->t);
-                a.line_n1 = line_at(h, h->t + 1);
-                a.line_out = line_at(h, h->t + 2);
-                source_fields(h, h->t + 2, a.src_E, a.src_H);
+    const bool pairs = h->fuse == 2 && h->g.mode == 2 && h->g.storage == LBEM_F32 && !h->analytic &&
+                       !h->mu_on && step2_worthwhile(h->g.nx, h->g.ny, h->g.nz);
+    StepArgs a2;
+    if (pairs) fill_common_args(h, a2);
+    for (int64_t k = 0; k < n;) {
+        if (pairs && n - k >= 2) {
+            // two steps in one pass: level n from f[cur], level n+2 into f[cur ^ 1]
+            if (h->xs_cnt + 2 > kXStage) {
+                const int rc = flush_x_stage(h);
+                if (rc != LBEM_OK) return rc;
             }
-            a.tn = h->t;
-            if (h->analytic)
-                for (int k = 0; k < 2; ++k) {
-                    const int64_t ts = h->t + k;
-                    const double ph = 2.0 * M_PI * (double)(ts % h->T) / (double)h->T;  // w t_s mod 2 pi
-                    a.pw_wt[k] = make_float2((float)std::cos(ph), (float)std::sin(ph));
-                    a.pw_t[k] = (float)ts;
-                }
-            a.dft_on = (h->faces.nfaces > 0 && h->dft_t0 >= 1 && t >= h->dft_t0 &&
-                        t < h->dft_t0 + (int64_t)h->dft_periods * h->T);
-            if (a.dft_on) {
-                const double ph = 2.0 * M_PI * (double)(t % h->T) / (double)h->T;
-                a.dft_c = std::cos(ph);
-                a.dft_s = std::sin(ph);
-                a.dft_scale = 2.0 / ((double)h->dft_periods * h->T);  // line (FP32, unscaled)
-                a.dft_scale_cells = a.dft_scale * h->scale;            // lattice (storage units)
-                a.dft_sc = a.dft_scale_cells * a.dft_c;
-                a.dft_ss = a.dft_scale_cells * a.dft_s;
+            step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
+            step_args_at(h, a2, h->t + 1, h->cur ^ 1, h->cur ^ 1);
+            stage_slot(h, a, h->xs_allmask);
+            stage_slot(h, a2, h->xs_allmask);
+            cudaError_t e = launch_step2(a, a2, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "two-step kernel launch");
+            h->launches += a.line_on ? 2 : 1;
+            h->cur ^= 1;
+            h->t += 2;
+            k += 2;
+        } else {
+            // a single step updates the faces it does not stage in place, so
+            // terms staged for them by two-step passes go in first
+            if (h->xs_wide) {
+                const int rc = flush_x_stage(h);
+                if (rc != LBEM_OK) return rc;
             }
+            step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
+            stage_slot(h, a, h->xs_xmask);
+            cudaError_t e = h->analytic ? launch_step_analytic(h->g.mode, h->g.storage, a, h->stream)
+                            : h->mu_on  ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
+                                        : launch_step(h->g.mode, h->g.storage, a, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+            h->launches += 1;
+            h->cur ^= 1;
+            h->t += 1;
+            k += 1;
         }
-        a.xstage = nullptr;
-        if (a.dft_on && h->xs_n > 0) {
-            a.xstage = h->xstage + (size_t)h->xs_cnt * h->NC * h->xs_n;
-            a.xs_n = h->xs_n;
-            h->xs_sc[h->xs_cnt] = a.dft_sc;
-            h->xs_ss[h->xs_cnt] = a.dft_ss;
-        }
-        cudaError_t e = h->analytic ? launch_step_analytic(h->g.mode, h->g.storage, a, h->stream)
-                        : h->mu_on  ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
-                                    : launch_step(h->g.mode, h->g.storage, a, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
-        h->launches += 1;
-        h->cur ^= 1;
-        h->t = t;
-        if (a.xstage && ++h->xs_cnt == kXStage) {
+        if (h->xs_cnt == kXStage) {
             const int rc = flush_x_stage(h);
             if (rc != LBEM_OK) return rc;
         }
     }
     return flush_x_stage(h);  // every call leaves the DFT complete
+}
+
+int32_t lbem_set_step_fusion(lbem_handle h, int32_t steps_per_pass)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (steps_per_pass != 1 && steps_per_pass != 2)
+        return fail(h, LBEM_ERR_ARG, "steps_per_pass must be 1 or 2");
+    h->fuse = steps_per_pass;
+    return LBEM_OK;
 }
 
 // ------------------------------------------------------------ batched runs

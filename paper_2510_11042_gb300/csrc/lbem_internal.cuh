@@ -213,8 +213,9 @@ struct StepArgs {
     double dft_scale;          // 2/(P T): incident line (FP32 units)
     double dft_scale_cells;    // 2/(P T) times the storage scale: lattice cells
     double dft_sc, dft_ss;     // dft_scale_cells times cos, sin of the step's phase
-    float *xstage;             // 3D, non-NULL: x-face fields go here ([NC][xs_n]) for dft_flush_x
-    long long xs_n;            // cells of the two x faces
+    float *xstage;             // 3D, non-NULL: staged face fields go here ([NC][xs_n]) for dft_flush_x
+    long long xs_n;            // cells of all faces (one component of one staged step)
+    long long xs_start[kMaxFaces];  // first staged cell of each face
     int nt_lo[3], nt_hi[3];
     double *dft;
     long long face_off[kMaxFaces];
@@ -268,6 +269,12 @@ cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cu
 cudaError_t launch_barrier_selftest(const BatchArgs &b, cudaStream_t s);
 int batch_max_blocks_per_sm(int mode, int storage);
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
+// Two steps in one pass (3D, FP32 storage, no mu_r map or closed-form source):
+// s1 the first step's arguments (reads fin_q), s2 the second's (writes fout_q,
+// which must not alias s1.fin_q); with the incident line on, a one-block
+// launch before it updates the line for both steps (two launches in all).
+cudaError_t launch_step2(const StepArgs &s1, const StepArgs &s2, cudaStream_t s);
+bool step2_worthwhile(int nx, int ny, int nz);
 // The step kernel with a per-cell mu_r (a.inv_mu), Eq. 2's h_0 = (mu_r - 1) H
 cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_t s);
 // The step kernel with the analytic plane-wave source (a.tfsf == 2; reads a.inv_mu)
@@ -300,16 +307,19 @@ struct FaceGeom {
     int lo[3], hi[3];
 };
 
-// Deferred DFT of the two x faces of the NTFF box: kXStage steps of staged
-// fields [step][NC][xs_n] and their phase coefficients.
+// Deferred DFT of NTFF faces: kXStage steps of staged fields [step][NC][n]
+// (n the cells of all faces, face f from start[f]), the faces each step
+// staged, and the steps' phase coefficients.
 constexpr int kXStage = 16;
 struct DftFlushArgs {
     const float *stage;
-    long long n;               // cells of the two x faces (side-major, then [nu][nv])
-    long long plane;           // nu * nv of one x face
-    int nc, cnt;
+    long long n;
+    int nc, cnt, nfaces;
     double *dft;
-    long long face_off[2];
+    long long start[kMaxFaces + 1];
+    long long plane[kMaxFaces];     // nu * nv of each face
+    long long face_off[kMaxFaces];
+    unsigned mask[kXStage];
     double sc[kXStage], ss[kXStage];
 };
 cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s);

@@ -51,6 +51,8 @@
 // tensor-core path applies.
 #include <type_traits>
 
+#include <algorithm>
+
 #include "lbem_internal.cuh"
 
 namespace lbem {
@@ -305,9 +307,9 @@ struct FloatCell {
 // Values are in storage units (population / scale); fields go to the DFT
 // multiplied back by the scale (dft_scale_cells), the incident source is
 // divided by it.
-template <int MODE, bool REC = false, bool MU = false, bool ANA = false, class Cell>
+template <int MODE, bool REC = false, bool MU = false, bool ANA = false, bool ALLSTAGE = false, class Cell>
 __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float inv_eps,
-                                            const StepArgs &a, float inv_mu = 1.0f)
+                                            const StepArgs &a, float inv_mu = 1.0f, bool surface = true)
 {
     using PL = Planes<MODE>;
     using M = Mode<MODE>;
@@ -340,7 +342,14 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
         H[c3] = MU ? B[c3] * inv_mu : B[c3];
     }
 
-    if (a.dft_on && in_box(x, y, z, a.nt_lo, a.nt_hi)) {
+    bool on_face = surface && a.dft_on && in_box(x, y, z, a.nt_lo, a.nt_hi);
+    if constexpr (ALLSTAGE) {
+        // the two-step kernel is issue-bound: keep the cells inside the box out
+        // of the face loop
+        on_face = on_face && (x == a.nt_lo[0] || x == a.nt_hi[0] || y == a.nt_lo[1] || y == a.nt_hi[1] ||
+                              z == a.nt_lo[2] || z == a.nt_hi[2]);
+    }
+    if (on_face) {
         const int g[3] = {x, y, z};
         const int n3[3] = {a.nx, a.ny, a.nz};
         float vals[PL::NC];
@@ -356,13 +365,22 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
                 const int ua = ax == 2 ? 1 : 2, va = ax == 0 ? 1 : 0;
                 const int iu = g[ua] - a.nt_lo[ua], iv = g[va] - a.nt_lo[va];
                 const int nu = a.face_nu[face], nv = a.face_nv[face];
-                if constexpr (MODE == 2) {
+                // Staged faces store the fields and dft_flush_x sums them in full
+                // warps (3D only: in 2D the branch cost more than it saved).  The
+                // single step stages the x faces, which hold two cells per row, one
+                // thread in a warp, whose read-modify-write would hold the warp for
+                // a DRAM round trip and a lone FP64 pass; the two-step kernel
+                // (ALLSTAGE) stages every face, since there the stall would hold
+                // a whole tile at every plane.
+                if constexpr (MODE == 2 && ALLSTAGE) {
+                    if (a.xstage) {
+                        const long long j = a.xs_start[face] + (long long)iu * nv + iv;
+#pragma unroll
+                        for (int k = 0; k < PL::NC; ++k) a.xstage[(long long)k * a.xs_n + j] = vals[k];
+                        continue;
+                    }
+                } else if constexpr (MODE == 2) {
                     if (ax == 0 && a.xstage) {
-                        // x faces hold two cells per row, one thread in a warp:
-                        // their read-modify-write would hold the warp for a DRAM
-                        // round trip and a lone FP64 pass, so they store the
-                        // fields and dft_flush_x sums them in full warps (3D
-                        // only: in 2D the branch cost more than it saved)
                         const long long j = ((long long)side * nu + iu) * nv + iv;
 #pragma unroll
                         for (int k = 0; k < PL::NC; ++k) a.xstage[(long long)k * a.xs_n + j] = vals[k];
@@ -787,25 +805,205 @@ __global__ void line_init_kernel(const StepArgs a)
 }
 
 
-// Sums cnt staged steps of x-face fields into the FP64 DFT accumulators in
-// step order, with the same fma as the direct path: one thread per (cell,
-// component), reads coalesced along the cells.
+
+// ---------------------------------------------------------------------------
+// Two steps per pass over HBM (3D, FP32 storage, plain update): temporal
+// blocking in the 2.5D form.  A block owns an xy tile of kT2X x kT2Y cells
+// and marches through z.  For each plane p it first computes level n+1 (the
+// state after the first step) of the tile and of its four edge halos (one
+// cell beyond each side, no corners: D3Q7 has no diagonal pulls) into shared
+// memory, then the second step of plane p-1 reads its pulls from there: the
+// rest and +-x, +-y groups of plane p-1 (tile and halos), the +z group of
+// plane p-2 and the -z group of plane p.  Level n is read from HBM and level
+// n+2 written to it once per two steps.  A halo cell needs only the group of
+// the direction that points into the tile, but costs a full update (its
+// moments need all 42 pulls); it skips the DFT, which the tile owning the cell
+// records.  Pulls that clamp at the domain edge read the cell's own value, so
+// halos are only computed inside the domain.  The arithmetic of every update
+// is the single-step kernel's (update_cell), so both paths give the same bits.
+constexpr int kT2X = 32, kT2Y = 8;
+constexpr int kT2Int = kT2X * kT2Y;               // 256 tile cells
+constexpr int kT2Halo = 2 * kT2Y + 2 * kT2X;      // 80 edge-halo cells
+constexpr int kT2Threads = 352;                   // 256 + 80, rounded up to whole warps
+constexpr int kT2A = 5 * 6 * kT2Int;              // groups of directions 0..4 of one plane
+constexpr int kT2H = 6 * kT2Halo;                 // halo groups of one plane
+constexpr int kT2F = 6 * kT2Int;                  // one +z or -z group of one plane
+constexpr size_t kT2Smem = (size_t)(2 * kT2A + 2 * kT2H + 3 * kT2F + kT2F) * sizeof(float);
+
+// Halo cell h of a tile at (x0, y0): its coordinates and the direction whose
+// group the tile pulls from it (h < 8: x0-1 (+x), < 16: x0+kT2X (-x), < 48:
+// y0-1 (+y), else y0+kT2Y (-y)).
+__device__ __forceinline__ void t2_halo(int h, int x0, int y0, int &x, int &y, int &dir)
+{
+    if (h < kT2Y) { x = x0 - 1; y = y0 + h; dir = 1; }
+    else if (h < 2 * kT2Y) { x = x0 + kT2X; y = y0 + h - kT2Y; dir = 2; }
+    else if (h < 2 * kT2Y + kT2X) { x = x0 + h - 2 * kT2Y; y = y0 - 1; dir = 3; }
+    else { x = x0 + h - 2 * kT2Y - kT2X; y = y0 + kT2Y; dir = 4; }
+}
+
+__device__ __forceinline__ void t2_src(const StepArgs &a, int x, int y, int z, int src[7])
+{
+    const int pz = a.ny * a.nxp;
+    const int c = z * pz + y * a.nxp + x;
+    src[0] = c;
+    src[1] = c - (x > 0 ? 1 : 0);
+    src[2] = c + (x < a.nx - 1 ? 1 : 0);
+    src[3] = c - (y > 0 ? a.nxp : 0);
+    src[4] = c + (y < a.ny - 1 ? a.nxp : 0);
+    src[5] = c - (z > 0 ? pz : 0);
+    src[6] = c + (z < a.nz - 1 ? pz : 0);
+}
+
+struct Step2Args {
+    StepArgs s1, s2;   // the two steps: s1 reads level n (fin_q), s2 writes level n+2 (fout_q)
+    int zc;            // planes per z chunk (blockIdx.z)
+};
+
+__global__ void __launch_bounds__(kT2Threads, 2) step2_kernel(const __grid_constant__ Step2Args P)
+{
+    extern __shared__ float t2sm[];
+    float *A = t2sm;                 // [2 planes][5 dirs][6][256]
+    float *H = A + 2 * kT2A;         // [2 planes][6][80]
+    float *F5 = H + 2 * kT2H;        // [3 planes][6][256]: +z groups
+    float *F6 = F5 + 3 * kT2F;       // [6][256]: -z group of the plane last computed
+    const StepArgs &s1 = P.s1, &s2 = P.s2;
+    const int nx = s1.nx, ny = s1.ny, nz = s1.nz;
+    const int x0 = blockIdx.x * kT2X, y0 = blockIdx.y * kT2Y;
+    const int t = threadIdx.x;
+    constexpr int Q = Planes<2>::Q;
+
+    // z chunk of this block: planes [z0, z1), plus level n+1 of the planes just
+    // below and above it (recomputed, not recorded by the DFT)
+    const int z0 = blockIdx.z * P.zc, z1 = min(nz, z0 + P.zc);
+
+    // level n+1 of plane p into the shared slots of p
+    auto produce = [&](int p) {
+        const bool mine = p >= z0 && p < z1;
+        if (t < kT2Int) {
+            const int x = x0 + t % kT2X, y = y0 + t / kT2X;
+            if (x < nx && y < ny) {
+                int src[7];
+                t2_src(s1, x, y, p, src);
+                float f[Q];
+                load_cell<2, float>(s1, src, f);
+                FloatCell cell{f};
+                update_cell<2, false, false, false, true>(cell, x, y, p, __ldg(s1.inv_eps + src[0]), s1, 1.0f, mine);
+                float *Ap = A + (p & 1) * kT2A;
+#pragma unroll
+                for (int d = 0; d < 5; ++d)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) Ap[(d * 6 + k) * kT2Int + t] = f[slot_plane(2, d, k)];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    F5[((p % 3) * 6 + k) * kT2Int + t] = f[slot_plane(2, 5, k)];
+                    F6[k * kT2Int + t] = f[slot_plane(2, 6, k)];
+                }
+            }
+        } else if (t < kT2Int + kT2Halo) {
+            const int h = t - kT2Int;
+            int x, y, dir;
+            t2_halo(h, x0, y0, x, y, dir);
+            if (x >= 0 && x < nx && y >= 0 && y < ny) {
+                int src[7];
+                t2_src(s1, x, y, p, src);
+                float f[Q];
+                load_cell<2, float>(s1, src, f);
+                FloatCell cell{f};
+                update_cell<2, false, false, false, true>(cell, x, y, p, __ldg(s1.inv_eps + src[0]), s1, 1.0f, false);
+                float *Hp = H + (p & 1) * kT2H;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const float v = dir == 1 ? f[slot_plane(2, 1, k)] : dir == 2 ? f[slot_plane(2, 2, k)]
+                                  : dir == 3 ? f[slot_plane(2, 3, k)] : f[slot_plane(2, 4, k)];
+                    Hp[k * kT2Halo + h] = v;
+                }
+            }
+        }
+    };
+
+    if (z0 > 0) produce(z0 - 1);   // for the +z group pulled by plane z0
+    produce(z0);
+    for (int z = z0; z < z1; ++z) {
+        if (z + 1 < nz) produce(z + 1);
+        __syncthreads();
+        // level n+2 of plane z
+        if (t < kT2Int) {
+            const int tx = t % kT2X, ty = t / kT2X;
+            const int x = x0 + tx, y = y0 + ty;
+            if (x < nx && y < ny) {
+                const float *Az = A + (z & 1) * kT2A, *Hz = H + (z & 1) * kT2H;
+                const float *F5z = F5 + ((z > 0 ? z - 1 : 0) % 3) * kT2F;
+                // shared index of direction d's pull: the tile, a halo, or the cell itself (clamped)
+                int ia[5];
+                const float *ba[5];
+                ia[0] = t; ba[0] = Az;
+                if (x > 0 && tx == 0) { ba[1] = Hz; ia[1] = ty; }
+                else { ba[1] = Az + 1 * 6 * kT2Int; ia[1] = x > 0 ? t - 1 : t; }
+                if (x < nx - 1 && tx == kT2X - 1) { ba[2] = Hz; ia[2] = kT2Y + ty; }
+                else { ba[2] = Az + 2 * 6 * kT2Int; ia[2] = x < nx - 1 ? t + 1 : t; }
+                if (y > 0 && ty == 0) { ba[3] = Hz; ia[3] = 2 * kT2Y + tx; }
+                else { ba[3] = Az + 3 * 6 * kT2Int; ia[3] = y > 0 ? t - kT2X : t; }
+                if (y < ny - 1 && ty == kT2Y - 1) { ba[4] = Hz; ia[4] = 2 * kT2Y + kT2X + tx; }
+                else { ba[4] = Az + 4 * 6 * kT2Int; ia[4] = y < ny - 1 ? t + kT2X : t; }
+                float f[Q];
+#pragma unroll
+                for (int d = 0; d < 5; ++d) {
+                    const int stride = (ba[d] == Hz) ? kT2Halo : kT2Int;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) f[slot_plane(2, d, k)] = ba[d][k * stride + ia[d]];
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    f[slot_plane(2, 5, k)] = F5z[k * kT2Int + t];
+                    f[slot_plane(2, 6, k)] = F6[k * kT2Int + t];
+                }
+                const int c = z * ny * s2.nxp + y * s2.nxp + x;
+                FloatCell cell{f};
+                update_cell<2, false, false, false, true>(cell, x, y, z, __ldg(s2.inv_eps + c), s2, 1.0f, true);
+                store_cell<2, float>(s2, c, f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The incident line for both steps of a fused pair, in one block: the line
+// work of step n (DFT at n+1, line(n+2)), then of step n+1 (DFT at n+2,
+// line(n+3)).
+template <int MODE>
+__global__ void line2_kernel(const __grid_constant__ Step2Args P)
+{
+    for (int s = threadIdx.x; s < P.s1.n_line; s += blockDim.x) line_work<MODE>(P.s1, s);
+    __syncthreads();
+    for (int s = threadIdx.x; s < P.s2.n_line; s += blockDim.x) line_work<MODE>(P.s2, s);
+}
+
+// Sums cnt staged steps of face fields into the FP64 DFT accumulators in step
+// order, with the same fma as the direct path: one thread per (face cell,
+// component), reads coalesced along the cells.  Slot s holds the faces in
+// mask[s].
 __global__ void dft_flush_x_kernel(const DftFlushArgs a)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n * a.nc) return;
     const long long j = i % a.n;
     const int k = (int)(i / a.n);
-    const int side = (int)(j / a.plane);
-    double *base = a.dft + a.face_off[side] + (j - side * a.plane);
-    double re = base[(2 * k + 0) * a.plane], im = base[(2 * k + 1) * a.plane];
+    int f = 0;
+    while (f + 1 < a.nfaces && j >= a.start[f + 1]) ++f;
+    unsigned any = 0;
+    for (int s = 0; s < a.cnt; ++s) any |= (a.mask[s] >> f) & 1u;
+    if (!any) return;
+    const long long r = j - a.start[f];
+    double *base = a.dft + a.face_off[f] + r;
+    double re = base[(2 * k + 0) * a.plane[f]], im = base[(2 * k + 1) * a.plane[f]];
     for (int s = 0; s < a.cnt; ++s) {
+        if (!((a.mask[s] >> f) & 1u)) continue;
         const double v = (double)a.stage[((long long)s * a.nc + k) * a.n + j];
         re = fma(v, a.sc[s], re);
         im = fma(v, -a.ss[s], im);
     }
-    base[(2 * k + 0) * a.plane] = re;
-    base[(2 * k + 1) * a.plane] = im;
+    base[(2 * k + 0) * a.plane[f]] = re;
+    base[(2 * k + 1) * a.plane[f]] = im;
 }
 
 template <int MODE, class S, bool REC = false, bool MU = false, bool ANA = false>
@@ -892,6 +1090,45 @@ cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s)
     const long long total = a.n * a.nc;
     dft_flush_x_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_step2(const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+{
+    if (s1.nz < 2 || s1.nx < 1 || s1.ny < 1) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(step2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kT2Smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    Step2Args P;
+    P.s1 = s1;
+    P.s2 = s2;
+    if (s1.line_on) {
+        line2_kernel<2><<<1, 512, 0, s>>>(P);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // z chunks: about two waves of blocks (2 per SM), chunks of at least 16
+    // planes (each costs two extra planes of level n+1)
+    const long long tiles = (long long)((s1.nx + kT2X - 1) / kT2X) * ((s1.ny + kT2Y - 1) / kT2Y);
+    int nzc = (int)std::min<long long>((4LL * 152 + tiles - 1) / tiles, std::max(1, s1.nz / 16));
+    nzc = std::max(1, nzc);
+    P.zc = (s1.nz + nzc - 1) / nzc;
+    nzc = (s1.nz + P.zc - 1) / P.zc;
+    const dim3 grid((s1.nx + kT2X - 1) / kT2X, (s1.ny + kT2Y - 1) / kT2Y, nzc);
+    step2_kernel<<<grid, kT2Threads, kT2Smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+// Whether two-step passes pay on this grid: their blocks (tiles x z chunks)
+// must fill at least one wave of 2 blocks per SM.
+bool step2_worthwhile(int nx, int ny, int nz)
+{
+    const long long tiles = (long long)((nx + kT2X - 1) / kT2X) * ((ny + kT2Y - 1) / kT2Y);
+    const long long chunks = std::max(1, nz / 16);
+    return nz >= 2 && tiles * chunks >= 2LL * 152;
 }
 
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s)

@@ -78,6 +78,7 @@ _SIGS = {
     "lbem_far_field": (_I32, [_P, _P, _P, _I32, _P, _P]),
     "lbem_incident_amplitude": (_I32, [_P, ctypes.POINTER(ctypes.c_double)]),
     "lbem_set_far_field_precision": (_I32, [_P, _I32]),
+    "lbem_set_step_fusion": (_I32, [_P, _I32]),
     "lbem_get_populations": (_I32, [_P, _P, _I32]),
     "lbem_set_populations": (_I32, [_P, _P, _I32]),
     "lbem_fields": (_I32, [_P, _P, _P, _I32]),
@@ -242,6 +243,10 @@ FAR_FIELD_PRECISION = {"mixed": LBEM_FAR_FIELD_MIXED, "fp64": LBEM_FAR_FIELD_FP6
 
 def lbem_set_far_field_precision(h, precision):
     _check(lib().lbem_set_far_field_precision(h, int(FAR_FIELD_PRECISION.get(precision, precision))), h)
+
+
+def lbem_set_step_fusion(h, steps_per_pass: int):
+    _check(lib().lbem_set_step_fusion(h, int(steps_per_pass)), h)
 
 
 def lbem_incident_amplitude(h) -> float:
@@ -547,6 +552,11 @@ class Solver:
 
     def far_field(self, theta, phi=None, with_amplitudes=False):
         return lbem_far_field(self.h, theta, phi, with_amplitudes)
+
+    def set_step_fusion(self, steps_per_pass):
+        """2 (default): two steps per pass over the populations where supported
+        and worthwhile (3D FP32); 1: single steps."""
+        lbem_set_step_fusion(self.h, steps_per_pass)
 
     def set_far_field_precision(self, precision):
         """"mixed" (FP32 contraction, FP64 sums above row chunks; default) or "fp64"."""

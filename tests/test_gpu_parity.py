@@ -353,3 +353,53 @@ def test_dft_same_for_any_step_split(mode):
     got = np.concatenate([f["data"].ravel() for f in faces])
     exp = np.concatenate([f.ravel() for f in ref])
     assert rel_l2(got, exp) <= TOL
+
+
+@pytest.mark.parametrize("shape,seed,wave", [((300, 130, 40), 3, False), ((350, 121, 33), 4, False),
+                                             ((256, 168, 40), 5, True)])
+def test_two_step_fusion_matches_single_steps(shape, seed, wave):
+    """lbem_set_step_fusion(2): the fused two-step kernel (shared-memory
+    intermediate level, edge halos, clamped pulls at the domain edges, z
+    chunks) gives the same populations and DFT accumulators as single steps,
+    bit for bit, over an odd step count that crosses the DFT window; on tiles
+    and chunks that do and do not divide the grid (32 x 8 cells).  The grids
+    are large enough for the pass to be taken (one wave of blocks)."""
+    if wave:
+        nx, ny, nz = shape
+        eps = np.ones((nz, ny, nx), np.float32)
+        zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        eps[(xx - nx / 2) ** 2 + (yy - ny / 2) ** 2 + (zz - nz / 2) ** 2 < 8.0 ** 2] = 2.0
+        wv = W.axis_wave("3d", shape, 4, 10.0, gap_ntff=2, gap_tf=2)
+        p = W.Problem("fuse_wave", "3d", shape, eps, 4, 0.3, wv, 60, 1)
+        init, steps = None, 45
+    else:
+        eps = W.random_eps(shape, 1.0, 6.0, seed)
+        p = W.Problem("fuse", "3d", shape, eps, 3, 0.3, None, 9, 1)
+        init, steps = W.random_state("3d", shape, seed), 9
+    a = gpu_solver(p, init=init, steps=0)
+    a.set_step_fusion(1)
+    b = gpu_solver(p, init=init, steps=0)
+    b.set_step_fusion(2)
+    if wave:
+        a.set_dft_window(20, 1)
+        b.set_dft_window(20, 1)
+    a.step(steps)
+    b.step(steps - 4)
+    b.step(4)
+    assert a.time == b.time == steps
+    assert np.array_equal(a.populations(), b.populations())
+    if wave:
+        assert np.array_equal(a.dft(), b.dft())
+        assert np.abs(a.dft()).max() > 0
+        assert a.incident_amplitude() == b.incident_amplitude()
+        th, ph = angles("3d")
+        assert np.array_equal(a.far_field(th, ph), b.far_field(th, ph))
+    from oracle import lb
+    if not wave:
+        lat = lb.Lattice(shape, p.eps, sponge_w=3, sigma_max=0.3)
+        lat.f = planes_to_oracle(init.astype(np.float64), "3d")
+        for n in range(steps):
+            lat.step(n)
+        assert rel_l2(b.populations(), oracle_to_planes(lat.f, "3d", shape)) <= TOL
+    with pytest.raises(Exception):
+        b.set_step_fusion(3)
