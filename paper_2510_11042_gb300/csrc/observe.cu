@@ -793,14 +793,19 @@ static cudaError_t launch_far_field_f32(FarFieldArgs a, cudaStream_t s, int *lau
     a.n_ang_pad = (a.n_ang + kF32Angles - 1) / kF32Angles * kF32Angles;
     const int ne = (a.g.hi[0] - a.g.lo[0] + 1) + (a.g.hi[1] - a.g.lo[1] + 1) + (a.g.hi[2] - a.g.lo[2] + 1);
     if (off > a.x32_cap || (long long)ne * a.n_ang_pad > a.tab32_cap) return cudaErrorInvalidValue;
-    // resident blocks per SM for each chunk height (shared memory grows with uc)
+    // resident blocks per SM for each chunk height (shared memory grows with
+    // uc), and the shared-memory opt-in: once per device
     constexpr int kMaxUc = 512;
-    static int sms = 0, per_uc[kMaxUc / kF32Rows + 1];
-    cudaError_t e = cudaSuccess;
-    if (sms == 0) {
-        int dev = 0, n = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    constexpr int kDevs = 64;
+    static int sms_of[kDevs], per_uc_of[kDevs][kMaxUc / kF32Rows + 1];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= kDevs) return cudaErrorInvalidDevice;
+    int *per_uc = per_uc_of[dev];
+    if (sms_of[dev] == 0) {
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(far_field_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)ff32_smem(kMaxUc));
@@ -808,8 +813,9 @@ static cudaError_t launch_far_field_f32(FarFieldArgs a, cudaStream_t s, int *lau
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_uc[uc / kF32Rows], far_field_f32,
                                                                kF32Threads, ff32_smem(uc));
         if (e != cudaSuccess) return e;
-        sms = n;
+        sms_of[dev] = n;
     }
+    const int sms = sms_of[dev];
     const int tiles = a.n_ang_pad / kF32Angles;
     int best_uc = 0;
     double best = 0.0;

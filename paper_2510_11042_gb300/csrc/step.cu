@@ -1095,19 +1095,22 @@ cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s)
 cudaError_t launch_step2(const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
 {
     if (s1.nz < 2 || s1.nx < 1 || s1.ny < 1) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(step2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kT2Smem);
+    // the shared-memory opt-in, once per device
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
+        e = cudaFuncSetAttribute(step2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT2Smem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        if (dev < 64) attr_set |= 1ull << dev;
     }
     Step2Args P;
     P.s1 = s1;
     P.s2 = s2;
     if (s1.line_on) {
         line2_kernel<2><<<1, 512, 0, s>>>(P);
-        cudaError_t e = cudaGetLastError();
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     // z chunks: about two waves of blocks (2 per SM), chunks of at least 16
