@@ -801,10 +801,14 @@ int32_t lbem_step(lbem_handle h, int64_t n)
             }
             step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
             step_args_at(h, a2, h->t + 1, h->cur ^ 1, h->cur ^ 1);
+            const int cnt0 = h->xs_cnt;
             stage_slot(h, a, h->xs_allmask);
             stage_slot(h, a2, h->xs_allmask);
             cudaError_t e = launch_step2(a, a2, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "two-step kernel launch");
+            if (e != cudaSuccess) {
+                h->xs_cnt = cnt0;   // the claimed slots hold nothing
+                return cuda_fail(h, e, "two-step kernel launch");
+            }
             h->launches += a.line_on ? 2 : 1;
             h->cur ^= 1;
             h->t += 2;
@@ -817,11 +821,15 @@ int32_t lbem_step(lbem_handle h, int64_t n)
                 if (rc != LBEM_OK) return rc;
             }
             step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
+            const int cnt0 = h->xs_cnt;
             stage_slot(h, a, h->xs_xmask);
             cudaError_t e = h->analytic ? launch_step_analytic(h->g.mode, h->g.storage, a, h->stream)
                             : h->mu_on  ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
                                         : launch_step(h->g.mode, h->g.storage, a, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+            if (e != cudaSuccess) {
+                h->xs_cnt = cnt0;
+                return cuda_fail(h, e, "step kernel launch");
+            }
             h->launches += 1;
             h->cur ^= 1;
             h->t += 1;
