@@ -5,7 +5,7 @@ a main lattice, a 1D incident line that feeds the total-field/scattered-field
 links, the running single-frequency DFT over the last steady-state period(s)
 (Sec. 2.4), and hands the recorded phasors to the NTFF of oracle/ntff.py.
 
-Readings of points the paper leaves open (each one also listed in the design doc):
+Readings of points the paper leaves open:
   * incident wave: link-wise TF/SF with the incident populations taken from a
     1D D3Q7 line along k_hat, driven at one node by the vacuum equilibrium of
     E0 ramp(t) sin(w t) p_hat (hard source), absorbing layers at both ends;
