@@ -203,15 +203,22 @@ int32_t lbem_set_permeability(lbem_handle h, const float *mu_r, int32_t mu_on_de
 int32_t lbem_far_field(lbem_handle h, const double *theta_host, const double *phi_host,
                        int32_t n, double *s2_host, double *amp_host);
 
-/* Temporal blocking: steps_per_pass = 2 (the default) lets lbem_step advance
- * 3D FP32 grids without a mu_r map or closed-form source two steps per pass
- * over the populations: a fused kernel keeps the intermediate state of each xy
- * tile (32 x 8 cells plus edge halos) in shared memory while it marches
- * through a chunk of z planes, bitwise the same result as two single steps.
- * It is taken where its blocks fill at least one wave (2 per SM); other grids,
- * and a last odd step, take single steps.  1 always takes single steps.
- * Anything else: LBEM_ERR_ARG. */
+/* Temporal blocking (Eq. 1 applied twice per pass over memory):
+ * steps_per_pass = 2 (the default) lets lbem_step advance 3D grids of any
+ * storage without a mu_r map or closed-form source two steps per pass over
+ * the populations: a fused kernel keeps the intermediate state of each xy tile
+ * (32 x 8 cells plus edge halos) in shared memory while it marches through a
+ * chunk of z planes, bitwise the same result as two single steps (16-bit
+ * storage rounds the intermediate state as a single step stores it).  It is
+ * taken where its blocks fill at least one wave of resident blocks; other
+ * grids, and a last odd step, take single steps.  1 always takes single
+ * steps.  Anything else: LBEM_ERR_ARG. */
 int32_t lbem_set_step_fusion(lbem_handle h, int32_t steps_per_pass);
+
+/* The steps per pass lbem_step takes on this handle as it is now configured:
+ * 2 where two-step passes apply (see lbem_set_step_fusion), else 1.
+ * NULL argument: LBEM_ERR_ARG. */
+int32_t lbem_get_step_fusion(lbem_handle h, int32_t *steps_per_pass);
 
 /* Precision of the 3D projection in lbem_far_field (2D is always FP64).
  * LBEM_FAR_FIELD_MIXED (the default): the FP32 contraction described above.

@@ -353,7 +353,7 @@ cudaError_t launch_adjoint_weights(const AdjWeightArgs &a, cudaStream_t s, int *
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long total = a.g.cell_start[a.g.nfaces];
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 16LL * std::max(1, sm_count()));
     adjoint_weights_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(a);
     *launches = 2;
     return cudaGetLastError();
@@ -363,7 +363,7 @@ cudaError_t launch_adjoint_finalize(const double *grad, const float *inv_eps, in
                                     int nxp, float *out, cudaStream_t s)
 {
     const long long n = (long long)nx * ny * nz;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 16LL * std::max(1, sm_count()));
     adjoint_finalize_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(grad, inv_eps, nx, ny, nz, nxp, out);
     return cudaGetLastError();
 }

@@ -167,8 +167,9 @@ static Layout make_layout(const lbem_grid_desc *g)
     const long long fx = (long long)g->ny * g->nz, fy = (long long)g->nx * g->nz,
                     fz = (long long)g->nx * g->ny;
     L.dft_doubles_max = (size_t)(2 * (fx + fy + (g->nz > 1 ? fz : 0))) * NC * 2;
-    L.scratch_doubles = std::max<size_t>((size_t)kAngleBatch * kMaxChunks * 12 + kAngleBatch * 16,
-                                         152 * 32 + 8);
+    // far-field partial sums; the energy monitor's block partials (capped at
+    // this size by launch_energy) share the region
+    L.scratch_doubles = (size_t)kAngleBatch * kMaxChunks * 12 + kAngleBatch * 16;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     L.f0 = take((size_t)L.Q * L.P * L.elem);
@@ -782,14 +783,21 @@ static void stage_slot(lbem_ctx *h, StepArgs &a, unsigned mask)
     ++h->xs_cnt;
 }
 
+// Whether lbem_step takes two steps per pass: fusion on, 3D without a mu_r
+// map or the closed-form source, on a grid whose blocks fill a wave.
+static bool two_step_passes(lbem_ctx *h)
+{
+    return h->fuse == 2 && h->g.mode == 2 && !h->analytic && !h->mu_on &&
+           step2_worthwhile(h->g.storage, h->g.nx, h->g.ny, h->g.nz);
+}
+
 int32_t lbem_step(lbem_handle h, int64_t n)
 {
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
     if (n < 0) return fail(h, LBEM_ERR_ARG, "n must be >= 0");
     StepArgs a;
     fill_common_args(h, a);
-    const bool pairs = h->fuse == 2 && h->g.mode == 2 && h->g.storage == LBEM_F32 && !h->analytic &&
-                       !h->mu_on && step2_worthwhile(h->g.nx, h->g.ny, h->g.nz);
+    const bool pairs = two_step_passes(h);
     StepArgs a2;
     if (pairs) fill_common_args(h, a2);
     for (int64_t k = 0; k < n;) {
@@ -804,7 +812,7 @@ int32_t lbem_step(lbem_handle h, int64_t n)
             const int cnt0 = h->xs_cnt;
             stage_slot(h, a, h->xs_allmask);
             stage_slot(h, a2, h->xs_allmask);
-            cudaError_t e = launch_step2(a, a2, h->stream);
+            cudaError_t e = launch_step2(h->g.storage, a, a2, h->stream);
             if (e != cudaSuccess) {
                 h->xs_cnt = cnt0;   // the claimed slots hold nothing
                 return cuda_fail(h, e, "two-step kernel launch");
@@ -849,6 +857,13 @@ int32_t lbem_set_step_fusion(lbem_handle h, int32_t steps_per_pass)
     if (steps_per_pass != 1 && steps_per_pass != 2)
         return fail(h, LBEM_ERR_ARG, "steps_per_pass must be 1 or 2");
     h->fuse = steps_per_pass;
+    return LBEM_OK;
+}
+
+int32_t lbem_get_step_fusion(lbem_handle h, int32_t *steps_per_pass)
+{
+    if (!h || !steps_per_pass) return fail(h, LBEM_ERR_ARG, "NULL argument");
+    *steps_per_pass = two_step_passes(h) ? 2 : 1;
     return LBEM_OK;
 }
 

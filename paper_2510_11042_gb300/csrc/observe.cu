@@ -4,6 +4,9 @@
 //   * the field-energy monitor (Sec. 3.2: steady state is checked by the total
 //     field energy) with its non-finite check;
 //   * fields of the stored state, permittivity upload, population pack/unpack.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "lbem_internal.cuh"
@@ -550,7 +553,8 @@ __global__ void sum_partials(const double *partial, int n, double *out)
 inline int grid_for(long long n, int threads)
 {
     long long b = (n + threads - 1) / threads;
-    if (b > 152 * 32) b = 152 * 32;
+    const long long cap = 32LL * std::max(1, sm_count());
+    if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
 
@@ -796,26 +800,29 @@ static cudaError_t launch_far_field_f32(FarFieldArgs a, cudaStream_t s, int *lau
     // resident blocks per SM for each chunk height (shared memory grows with
     // uc), and the shared-memory opt-in: once per device
     constexpr int kMaxUc = 512;
-    constexpr int kDevs = 64;
-    static int sms_of[kDevs], per_uc_of[kDevs][kMaxUc / kF32Rows + 1];
+    static std::mutex setup_mu;
+    static bool ready_of[kMaxDevices];
+    static int per_uc_of[kMaxDevices][kMaxUc / kF32Rows + 1];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= kDevs) return cudaErrorInvalidDevice;
-    int *per_uc = per_uc_of[dev];
-    if (sms_of[dev] == 0) {
-        int n = 0;
-        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const int sms = sm_count();
+    if (sms < 1) return cudaErrorInvalidDevice;
+    int per_uc[kMaxUc / kF32Rows + 1];
+    {
+        std::lock_guard<std::mutex> lock(setup_mu);
+        if (!ready_of[dev]) {
             e = cudaFuncSetAttribute(far_field_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)ff32_smem(kMaxUc));
-        for (int uc = kF32Rows; e == cudaSuccess && uc <= kMaxUc; uc += kF32Rows)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_uc[uc / kF32Rows], far_field_f32,
-                                                               kF32Threads, ff32_smem(uc));
-        if (e != cudaSuccess) return e;
-        sms_of[dev] = n;
+            for (int uc = kF32Rows; e == cudaSuccess && uc <= kMaxUc; uc += kF32Rows)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_uc_of[dev][uc / kF32Rows], far_field_f32,
+                                                                   kF32Threads, ff32_smem(uc));
+            if (e != cudaSuccess) return e;
+            ready_of[dev] = true;
+        }
+        std::memcpy(per_uc, per_uc_of[dev], sizeof per_uc);
     }
-    const int sms = sms_of[dev];
     const int tiles = a.n_ang_pad / kF32Angles;
     int best_uc = 0;
     double best = 0.0;

@@ -49,9 +49,12 @@
 // step: B_cell = 2 Q s + 4 bytes.  The update is a
 // memory-bound stencil (~1 flop/byte), so it runs on the CUDA cores; no
 // tensor-core path applies.
-#include <type_traits>
+#include <cuda.h>
 
 #include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
 
 #include "lbem_internal.cuh"
 
@@ -634,14 +637,13 @@ __device__ __forceinline__ void row_cells(const StepArgs &a, int bx, int y, int 
 // One block per tile of BX cells x R consecutive rows (y fastest, then z);
 // the first blocks also update the incident line.  R = rows_of<S> blocks of
 // several rows cut the per-block start-up cost of short 128-cell rows; grids
-// of under one wave of such blocks (152 SMs x 7) take one row per block
+// of under one wave of such blocks (7 per SM) take one row per block
 // instead (ONE), so that every SM gets work.  72 registers (7 blocks of 128
 // threads per SM) hold a cell without spilling; the 3D kernel with the
 // closed-form source (ANA) also holds the source terms and takes 96 (5 blocks:
 // 2.83 ms at 384^3, against 3.98 ms spilling at 7).  These were chosen by timing
 // the 384^3 sphere and 256^2 to 4096^2 EZ grids on GB300.
 template <class S> __host__ __device__ constexpr int rows_of() { return sizeof(S) == 4 ? 2 : 4; }
-constexpr long long kWaveBlocks = 152LL * 7;
 
 template <int MODE, class S, int BX, bool REC = false, bool MU = false, bool ANA = false, bool ONE = false>
 __global__ void __launch_bounds__(BX, (ANA && MODE == 2) ? 5 : 7) step_kernel_cell(const StepArgs a)
@@ -807,175 +809,526 @@ __global__ void line_init_kernel(const StepArgs a)
 
 
 // ---------------------------------------------------------------------------
-// Two steps per pass over HBM (3D, FP32 storage, plain update): temporal
-// blocking in the 2.5D form.  A block owns an xy tile of kT2X x kT2Y cells
-// and marches through z.  For each plane p it first computes level n+1 (the
-// state after the first step) of the tile and of its four edge halos (one
-// cell beyond each side, no corners: D3Q7 has no diagonal pulls) into shared
-// memory, then the second step of plane p-1 reads its pulls from there: the
-// rest and +-x, +-y groups of plane p-1 (tile and halos), the +z group of
-// plane p-2 and the -z group of plane p.  Level n is read from HBM and level
-// n+2 written to it once per two steps.  A halo cell needs only the group of
-// the direction that points into the tile, but costs a full update (its
-// moments need all 42 pulls); it skips the DFT, which the tile owning the cell
-// records.  Pulls that clamp at the domain edge read the cell's own value, so
-// halos are only computed inside the domain.  The arithmetic of every update
-// is the single-step kernel's (update_cell), so both paths give the same bits.
-constexpr int kT2X = 32, kT2Y = 8;
-constexpr int kT2Int = kT2X * kT2Y;               // 256 tile cells
-constexpr int kT2Halo = 2 * kT2Y + 2 * kT2X;      // 80 edge-halo cells
-constexpr int kT2Threads = 352;                   // 256 + 80, rounded up to whole warps
-constexpr int kT2A = 5 * 6 * kT2Int;              // groups of directions 0..4 of one plane
-constexpr int kT2H = 6 * kT2Halo;                 // halo groups of one plane
-constexpr int kT2F = 6 * kT2Int;                  // one +z or -z group of one plane
-constexpr size_t kT2Smem = (size_t)(2 * kT2A + 2 * kT2H + 3 * kT2F + kT2F) * sizeof(float);
+// Two steps per pass over HBM (3D, plain update; FP32, FP16 and BF16 storage):
+// temporal blocking in the 2.5D form, level n staged by the tensor-memory
+// accelerator (TMA).
+//
+// A block owns an xy tile of 32 x 8 cells and marches through a chunk of z
+// planes; each tile thread keeps one (x, y) column.  For every plane p:
+//   * level n+1 (the state after the first step) of the tile and of its four
+//     edge halos (one cell beyond each side, no corners: D3Q7 pulls along one
+//     axis at a time) is computed from a bundle of level-n boxes in shared
+//     memory: the rest, +-x and +-y groups of plane p, the +z group of plane
+//     p-1 and the -z group of plane p+1 (each z index clamped to the grid, the
+//     zero-gradient boundary of Eq. 4), all over the tile's 8 rows and one row
+//     on either side (the +y box one row lower, the -y box one row higher),
+//     and 1/eps_r of plane p;
+//   * level n+2 of plane p-1 is computed from level n+1: the +-x and +-y groups
+//     of plane p-1 from shared memory (tile and halo cells), its rest group,
+//     the +z group of plane p-2 and the -z group of plane p from the column's
+//     own registers, and written to HBM.
+// One elected thread copies the bundle of plane p+2 into the buffer plane p
+// has just released while the block computes, so loads stay in flight during
+// the arithmetic; bundles alternate between two buffers, each with an
+// mbarrier that the copies complete.  Level n+1 of the +-x, +-y groups lives in
+// three rotating slots, so one block barrier per plane orders everything.
+// Level n is read from HBM and level n+2 written once per two steps.  A halo
+// cell needs only the group of the direction that points into the tile but
+// costs a full update, and records no DFT (the tile owning the cell does).
+// Pulls that clamp at the domain edge read the cell's own value, so halo cells
+// outside the domain are never read.  Every update is update_cell, and with
+// 16-bit storage level n+1 is rounded to the storage type before it is used,
+// so the result is bitwise that of two single steps.
+namespace t2 {
+constexpr int TX = 32, TY = 8;
+constexpr int NT = TX * TY;              // tile cells
+constexpr int NHALO = 2 * TY + 2 * TX;   // edge-halo cells
+constexpr int THREADS = 352;             // NT + NHALO, rounded up to whole warps
+constexpr int ISSUER = NT + NHALO;       // an idle lane of the last warp issues the copies
+constexpr int ROWS = TY + 2;             // box rows
+constexpr int EPS_X0 = 4, EPS_W = 40;    // 1/eps_r box: 40 cells from x0 - 4 (16-byte aligned)
+constexpr int EPS_BYTES = ROWS * EPS_W * 4;
+__host__ __device__ constexpr int pad128(int b) { return (b + 127) / 128 * 128; }
+constexpr long long kWaitNs = 1000000000LL;  // a bounded wait gives up after 1 s
+}  // namespace t2
 
-// Halo cell h of a tile at (x0, y0): its coordinates and the direction whose
-// group the tile pulls from it (h < 8: x0-1 (+x), < 16: x0+kT2X (-x), < 48:
-// y0-1 (+y), else y0+kT2Y (-y)).
-__device__ __forceinline__ void t2_halo(int h, int x0, int y0, int &x, int &y, int &dir)
+// Shared-memory layout per storage type.  A bundle holds one box per
+// direction and 1/eps_r; a slot holds level n+1 of the +-x, +-y groups of the
+// tile cells and the one group of each halo cell.
+template <class S> struct T2L {
+    // 16-bit: per direction a quad (8 B) and a pair (4 B) per cell, boxes of
+    // 40 cells from x0 - 4 (a 4-byte pair's x coordinate must be a multiple of 4)
+    static constexpr int X0 = 4, W = 40;
+    static constexpr int QUAD_BYTES = t2::ROWS * W * 8, PAIR_BYTES = t2::ROWS * W * 4;
+    static constexpr int PAIR_OFF = t2::pad128(QUAD_BYTES);
+    static constexpr int DIR_BYTES = t2::pad128(PAIR_OFF + PAIR_BYTES);
+    static constexpr int EPS_OFF = 7 * DIR_BYTES;
+    static constexpr int BUNDLE = t2::pad128(EPS_OFF + t2::EPS_BYTES);
+    static constexpr unsigned TX_BYTES = 7 * (QUAD_BYTES + PAIR_BYTES) + t2::EPS_BYTES;
+    static constexpr int S_TQ = 0, S_TP = 4 * t2::NT * 8, S_HQ = S_TP + 4 * t2::NT * 4,
+                         S_HP = S_HQ + t2::NHALO * 8;
+    static constexpr int SLOT = S_HP + t2::NHALO * 4;
+    static constexpr int SMEM = 2 * BUNDLE + 3 * SLOT;
+    static constexpr int MIN_BLOCKS = 2;
+    static constexpr int CLUSTER_X = 1;
+};
+template <> struct T2L<float> {
+    // FP32: per direction three float2 groups, boxes of 36 cells from x0 - 2
+    static constexpr int X0 = 2, W = 36;
+    static constexpr int GROUP_BYTES = t2::ROWS * W * 8;
+    static constexpr int DIR_BYTES = t2::pad128(3 * GROUP_BYTES);
+    static constexpr int EPS_OFF = 7 * DIR_BYTES;
+    static constexpr int BUNDLE = t2::pad128(EPS_OFF + t2::EPS_BYTES);
+    static constexpr unsigned TX_BYTES = 7 * 3 * GROUP_BYTES + t2::EPS_BYTES;
+    static constexpr int S_TILE = 4 * 3 * t2::NT * 8;  // float2 [4 dirs][3][NT], then halo float2 [3][NHALO]
+    static constexpr int SLOT = S_TILE + 3 * t2::NHALO * 8;
+    static constexpr int SMEM = 2 * BUNDLE + 3 * SLOT;
+    static constexpr int MIN_BLOCKS = 1;
+    // launched in clusters of two x-adjacent tiles, with the boxes' L2 fetch
+    // granularity left at the default (measured at 384^3: 1.93 -> 1.71 ms per
+    // update with the evict-first stores); 16-bit storage measured faster
+    // without clusters and with 256-byte L2 promotion
+    static constexpr int CLUSTER_X = 2;
+};
+static_assert(T2L<float>::SMEM <= 232448, "two-step FP32 shared memory");
+static_assert(2 * (T2L<__half>::SMEM + 1024) <= 233472, "two 16-bit two-step blocks per SM");
+
+// The six values of one direction of a cell in storage form.
+template <class S> struct DirVal { uint2 q; unsigned p; };   // 16-bit: quad + pair
+template <> struct DirVal<float> { float2 g[3]; };
+
+template <class S>
+__device__ __forceinline__ DirVal<S> to_dir(const float *f, int d)
 {
-    if (h < kT2Y) { x = x0 - 1; y = y0 + h; dir = 1; }
-    else if (h < 2 * kT2Y) { x = x0 + kT2X; y = y0 + h - kT2Y; dir = 2; }
-    else if (h < 2 * kT2Y + kT2X) { x = x0 + h - 2 * kT2Y; y = y0 - 1; dir = 3; }
-    else { x = x0 + h - 2 * kT2Y - kT2X; y = y0 + kT2Y; dir = 4; }
+    DirVal<S> v;
+    if constexpr (sizeof(S) == 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v.g[k] = make_float2(f[slot_plane(2, d, 2 * k)], f[slot_plane(2, d, 2 * k + 1)]);
+    } else {
+        using IO = Io<S>;
+        v.q = make_uint2(IO::pack(f[slot_plane(2, d, 0)], f[slot_plane(2, d, 1)]),
+                         IO::pack(f[slot_plane(2, d, 2)], f[slot_plane(2, d, 3)]));
+        v.p = IO::pack(f[slot_plane(2, d, 4)], f[slot_plane(2, d, 5)]);
+    }
+    return v;
 }
 
-__device__ __forceinline__ void t2_src(const StepArgs &a, int x, int y, int z, int src[7])
+template <class S>
+__device__ __forceinline__ void from_dir(const DirVal<S> &v, float *f, int d)
 {
-    const int pz = a.ny * a.nxp;
-    const int c = z * pz + y * a.nxp + x;
-    src[0] = c;
-    src[1] = c - (x > 0 ? 1 : 0);
-    src[2] = c + (x < a.nx - 1 ? 1 : 0);
-    src[3] = c - (y > 0 ? a.nxp : 0);
-    src[4] = c + (y < a.ny - 1 ? a.nxp : 0);
-    src[5] = c - (z > 0 ? pz : 0);
-    src[6] = c + (z < a.nz - 1 ? pz : 0);
+    if constexpr (sizeof(S) == 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            f[slot_plane(2, d, 2 * k)] = v.g[k].x;
+            f[slot_plane(2, d, 2 * k + 1)] = v.g[k].y;
+        }
+    } else {
+        using IO = Io<S>;
+        const float2 a = IO::unpack(v.q.x), b = IO::unpack(v.q.y), c = IO::unpack(v.p);
+        f[slot_plane(2, d, 0)] = a.x;
+        f[slot_plane(2, d, 1)] = a.y;
+        f[slot_plane(2, d, 2)] = b.x;
+        f[slot_plane(2, d, 3)] = b.y;
+        f[slot_plane(2, d, 4)] = c.x;
+        f[slot_plane(2, d, 5)] = c.y;
+    }
+}
+
+// Direction d of the cell at box column col, row row of a bundle.
+template <class S>
+__device__ __forceinline__ DirVal<S> bundle_get(const unsigned char *buf, int d, int col, int row)
+{
+    using L = T2L<S>;
+    const unsigned char *b = buf + d * L::DIR_BYTES;
+    const int i = row * L::W + col;
+    DirVal<S> v;
+    if constexpr (sizeof(S) == 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v.g[k] = reinterpret_cast<const float2 *>(b + k * L::GROUP_BYTES)[i];
+    } else {
+        v.q = reinterpret_cast<const uint2 *>(b)[i];
+        v.p = reinterpret_cast<const unsigned *>(b + L::PAIR_OFF)[i];
+    }
+    return v;
+}
+
+// The pulled populations of the cell (x, y) at box column col, row row: the
+// clamped pull of Eqs. 1 and 4 in box coordinates (the +y box starts one row
+// higher, the -y box one row lower than the others).
+template <class S>
+__device__ __forceinline__ void bundle_cell(const unsigned char *buf, int col, int row, int x, int y, int nx,
+                                            int ny, float *f)
+{
+    from_dir<S>(bundle_get<S>(buf, 0, col, row), f, 0);
+    from_dir<S>(bundle_get<S>(buf, 1, x > 0 ? col - 1 : col, row), f, 1);
+    from_dir<S>(bundle_get<S>(buf, 2, x < nx - 1 ? col + 1 : col, row), f, 2);
+    from_dir<S>(bundle_get<S>(buf, 3, col, y > 0 ? row : row + 1), f, 3);
+    from_dir<S>(bundle_get<S>(buf, 4, col, y < ny - 1 ? row : row - 1), f, 4);
+    from_dir<S>(bundle_get<S>(buf, 5, col, row), f, 5);
+    from_dir<S>(bundle_get<S>(buf, 6, col, row), f, 6);
+}
+
+// Slot entries: direction d (1..4) of tile cell i, or the group of halo cell i.
+template <class S>
+__device__ __forceinline__ void slot_put(unsigned char *slot, bool halo, int d, int i, const DirVal<S> &v)
+{
+    using L = T2L<S>;
+    if constexpr (sizeof(S) == 4) {
+        float2 *b = reinterpret_cast<float2 *>(slot) + (halo ? 4 * 3 * t2::NT + i : (d - 1) * 3 * t2::NT + i);
+        const int st = halo ? t2::NHALO : t2::NT;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b[k * st] = v.g[k];
+    } else {
+        const int j = halo ? i : (d - 1) * t2::NT + i;
+        reinterpret_cast<uint2 *>(slot + (halo ? L::S_HQ : L::S_TQ))[j] = v.q;
+        reinterpret_cast<unsigned *>(slot + (halo ? L::S_HP : L::S_TP))[j] = v.p;
+    }
+}
+
+template <class S>
+__device__ __forceinline__ DirVal<S> slot_get(const unsigned char *slot, bool halo, int d, int i)
+{
+    using L = T2L<S>;
+    DirVal<S> v;
+    if constexpr (sizeof(S) == 4) {
+        const float2 *b =
+            reinterpret_cast<const float2 *>(slot) + (halo ? 4 * 3 * t2::NT + i : (d - 1) * 3 * t2::NT + i);
+        const int st = halo ? t2::NHALO : t2::NT;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v.g[k] = b[k * st];
+    } else {
+        const int j = halo ? i : (d - 1) * t2::NT + i;
+        v.q = reinterpret_cast<const uint2 *>(slot + (halo ? L::S_HQ : L::S_TQ))[j];
+        v.p = reinterpret_cast<const unsigned *>(slot + (halo ? L::S_HP : L::S_TP))[j];
+    }
+    return v;
+}
+
+// ---- TMA and mbarrier (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier; false if it has not completed
+// within t2::kWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > (unsigned long long)t2::kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
 }
 
 struct Step2Args {
-    StepArgs s1, s2;   // the two steps: s1 reads level n (fin_q), s2 writes level n+2 (fout_q)
-    int zc;            // planes per z chunk (blockIdx.z)
+    CUtensorMap map_a;    // FP32: the 21 float2 groups; 16-bit: the 7 quads
+    CUtensorMap map_b;    // 16-bit: the 7 pairs
+    CUtensorMap map_eps;  // 1/eps_r
+    StepArgs s1, s2;      // the two steps: s1 reads level n (fin_q), s2 writes level n+2 (fout_q)
+    int zc;               // planes per z chunk (blockIdx.z)
 };
 
-__global__ void __launch_bounds__(kT2Threads, 2) step2_kernel(const __grid_constant__ Step2Args P)
+// Copy the level-n bundle of plane p into the buffer at dst; the copies
+// complete the mbarrier bar.  Every x coordinate is x0 - X0 with x0 a
+// multiple of 32, so each box starts on a 16-byte boundary.
+template <class S>
+__device__ __forceinline__ void t2_issue(const Step2Args &P, uint32_t dst, uint32_t bar, int x0, int y0, int p, int nz)
 {
-    extern __shared__ float t2sm[];
-    float *A = t2sm;                 // [2 planes][5 dirs][6][256]
-    float *H = A + 2 * kT2A;         // [2 planes][6][80]
-    float *F5 = H + 2 * kT2H;        // [3 planes][6][256]: +z groups
-    float *F6 = F5 + 3 * kT2F;       // [6][256]: -z group of the plane last computed
-    const StepArgs &s1 = P.s1, &s2 = P.s2;
-    const int nx = s1.nx, ny = s1.ny, nz = s1.nz;
-    const int x0 = blockIdx.x * kT2X, y0 = blockIdx.y * kT2Y;
-    const int t = threadIdx.x;
-    constexpr int Q = Planes<2>::Q;
-
-    // z chunk of this block: planes [z0, z1), plus level n+1 of the planes just
-    // below and above it (recomputed, not recorded by the DFT)
-    const int z0 = blockIdx.z * P.zc, z1 = min(nz, z0 + P.zc);
-
-    // level n+1 of plane p into the shared slots of p
-    auto produce = [&](int p) {
-        const bool mine = p >= z0 && p < z1;
-        if (t < kT2Int) {
-            const int x = x0 + t % kT2X, y = y0 + t / kT2X;
-            if (x < nx && y < ny) {
-                int src[7];
-                t2_src(s1, x, y, p, src);
-                float f[Q];
-                load_cell<2, float>(s1, src, f);
-                FloatCell cell{f};
-                update_cell<2, false, false, false, true>(cell, x, y, p, __ldg(s1.inv_eps + src[0]), s1, 1.0f, mine);
-                float *Ap = A + (p & 1) * kT2A;
+    using L = T2L<S>;
+    const int pm = p > 0 ? p - 1 : 0, pp = p < nz - 1 ? p + 1 : nz - 1;
+    mbar_expect_tx(bar, L::TX_BYTES);
 #pragma unroll
-                for (int d = 0; d < 5; ++d)
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) Ap[(d * 6 + k) * kT2Int + t] = f[slot_plane(2, d, k)];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    F5[((p % 3) * 6 + k) * kT2Int + t] = f[slot_plane(2, 5, k)];
-                    F6[k * kT2Int + t] = f[slot_plane(2, 6, k)];
-                }
-            }
-        } else if (t < kT2Int + kT2Halo) {
-            const int h = t - kT2Int;
-            int x, y, dir;
-            t2_halo(h, x0, y0, x, y, dir);
-            if (x >= 0 && x < nx && y >= 0 && y < ny) {
-                int src[7];
-                t2_src(s1, x, y, p, src);
-                float f[Q];
-                load_cell<2, float>(s1, src, f);
-                FloatCell cell{f};
-                update_cell<2, false, false, false, true>(cell, x, y, p, __ldg(s1.inv_eps + src[0]), s1, 1.0f, false);
-                float *Hp = H + (p & 1) * kT2H;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const float v = dir == 1 ? f[slot_plane(2, 1, k)] : dir == 2 ? f[slot_plane(2, 2, k)]
-                                  : dir == 3 ? f[slot_plane(2, 3, k)] : f[slot_plane(2, 4, k)];
-                    Hp[k * kT2Halo + h] = v;
-                }
-            }
+    for (int d = 0; d < 7; ++d) {
+        const int yb = d == 3 ? y0 - 2 : (d == 4 ? y0 : y0 - 1);
+        const int zb = d == 5 ? pm : (d == 6 ? pp : p);
+        if constexpr (sizeof(S) == 4) {
+            tma_load_4d(dst + d * L::DIR_BYTES, &P.map_a, 2 * (x0 - L::X0), yb, zb, 3 * d, bar);
+        } else {
+            tma_load_4d(dst + d * L::DIR_BYTES, &P.map_a, 4 * (x0 - L::X0), yb, zb, d, bar);
+            tma_load_4d(dst + d * L::DIR_BYTES + L::PAIR_OFF, &P.map_b, 2 * (x0 - L::X0), yb, zb, d, bar);
         }
-    };
+    }
+    tma_load_3d(dst + L::EPS_OFF, &P.map_eps, x0 - t2::EPS_X0, y0 - 1, p, bar);
+}
 
-    if (z0 > 0) produce(z0 - 1);   // for the +z group pulled by plane z0
-    produce(z0);
-    for (int z = z0; z < z1; ++z) {
-        if (z + 1 < nz) produce(z + 1);
-        __syncthreads();
-        // level n+2 of plane z
-        if (t < kT2Int) {
-            const int tx = t % kT2X, ty = t / kT2X;
-            const int x = x0 + tx, y = y0 + ty;
-            if (x < nx && y < ny) {
-                const float *Az = A + (z & 1) * kT2A, *Hz = H + (z & 1) * kT2H;
-                const float *F5z = F5 + ((z > 0 ? z - 1 : 0) % 3) * kT2F;
-                // shared index of direction d's pull: the tile, a halo, or the cell itself (clamped)
-                int ia[5];
-                const float *ba[5];
-                ia[0] = t; ba[0] = Az;
-                if (x > 0 && tx == 0) { ba[1] = Hz; ia[1] = ty; }
-                else { ba[1] = Az + 1 * 6 * kT2Int; ia[1] = x > 0 ? t - 1 : t; }
-                if (x < nx - 1 && tx == kT2X - 1) { ba[2] = Hz; ia[2] = kT2Y + ty; }
-                else { ba[2] = Az + 2 * 6 * kT2Int; ia[2] = x < nx - 1 ? t + 1 : t; }
-                if (y > 0 && ty == 0) { ba[3] = Hz; ia[3] = 2 * kT2Y + tx; }
-                else { ba[3] = Az + 3 * 6 * kT2Int; ia[3] = y > 0 ? t - kT2X : t; }
-                if (y < ny - 1 && ty == kT2Y - 1) { ba[4] = Hz; ia[4] = 2 * kT2Y + kT2X + tx; }
-                else { ba[4] = Az + 4 * 6 * kT2Int; ia[4] = y < ny - 1 ? t + kT2X : t; }
-                float f[Q];
+// Halo cell h of a tile at (x0, y0): its coordinates and the direction whose
+// group the tile pulls from it (h < 8: x0-1 (+x), < 16: x0+32 (-x), < 48:
+// y0-1 (+y), else y0+8 (-y)).
+__device__ __forceinline__ void t2_halo(int h, int x0, int y0, int &x, int &y, int &dir)
+{
+    using namespace t2;
+    if (h < TY) { x = x0 - 1; y = y0 + h; dir = 1; }
+    else if (h < 2 * TY) { x = x0 + TX; y = y0 + h - TY; dir = 2; }
+    else if (h < 2 * TY + TX) { x = x0 + h - 2 * TY; y = y0 - 1; dir = 3; }
+    else { x = x0 + h - 2 * TY - TX; y = y0 + TY; dir = 4; }
+}
+
+// Store of level n+2 (3D): as store_cell, with an L2 evict-first policy,
+// since nothing reads these lines again in the launch and the boxes of the
+// next planes should keep the cache.
+__device__ __forceinline__ unsigned long long l2_evict_first()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+template <class S>
+__device__ __forceinline__ void store_cell_evict_first(const StepArgs &a, int c, const float *f)
+{
+    const unsigned long long pol = l2_evict_first();
 #pragma unroll
-                for (int d = 0; d < 5; ++d) {
-                    const int stride = (ba[d] == Hz) ? kT2Halo : kT2Int;
+    for (int i = 0; i < 7; ++i) {
+        void *const *b = a.fout_q + i * 6;
+        if constexpr (sizeof(S) == 4) {
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) f[slot_plane(2, d, k)] = ba[d][k * stride + ia[d]];
-                }
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    f[slot_plane(2, 5, k)] = F5z[k * kT2Int + t];
-                    f[slot_plane(2, 6, k)] = F6[k * kT2Int + t];
-                }
-                const int c = z * ny * s2.nxp + y * s2.nxp + x;
-                FloatCell cell{f};
-                update_cell<2, false, false, false, true>(cell, x, y, z, __ldg(s2.inv_eps + c), s2, 1.0f, true);
-                store_cell<2, float>(s2, c, f);
-            }
+            for (int k = 0; k < 3; ++k)
+                asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(
+                                 static_cast<float2 *>(b[2 * k]) + c),
+                             "f"(f[slot_plane(2, i, 2 * k)]), "f"(f[slot_plane(2, i, 2 * k + 1)]), "l"(pol)
+                             : "memory");
+        } else {
+            using IO = Io<S>;
+            asm volatile("st.global.L2::cache_hint.v2.b32 [%0], {%1, %2}, %3;" ::"l"(static_cast<uint2 *>(b[0]) + c),
+                         "r"(IO::pack(f[slot_plane(2, i, 0)], f[slot_plane(2, i, 1)])),
+                         "r"(IO::pack(f[slot_plane(2, i, 2)], f[slot_plane(2, i, 3)])), "l"(pol)
+                         : "memory");
+            asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(static_cast<unsigned *>(b[4]) + c),
+                         "r"(IO::pack(f[slot_plane(2, i, 4)], f[slot_plane(2, i, 5)])), "l"(pol)
+                         : "memory");
         }
-        __syncthreads();
     }
 }
+
+// Level n+2 of tile cell t at (x, y, z) from level n+1: the +-x, +-y groups
+// from the slot of plane z (a neighbour in the tile, a halo cell at the tile
+// edge, or the cell itself where the pull clamps at the domain edge), the
+// rest, +z and -z groups given.
+template <class S>
+__device__ __forceinline__ void t2_level2(const StepArgs &s2, const unsigned char *slot, int t, int x, int y, int z,
+                                          const DirVal<S> &d0, const DirVal<S> &d5, const DirVal<S> &d6, float ie)
+{
+    using namespace t2;
+    const int nx = s2.nx, ny = s2.ny;
+    const int tx = t % TX, ty = t / TX;
+    float f[Planes<2>::Q];
+    from_dir<S>(d0, f, 0);
+    {
+        const bool h = x > 0 && tx == 0;
+        from_dir<S>(slot_get<S>(slot, h, 1, h ? ty : (x > 0 ? t - 1 : t)), f, 1);
+    }
+    {
+        const bool h = x < nx - 1 && tx == TX - 1;
+        from_dir<S>(slot_get<S>(slot, h, 2, h ? TY + ty : (x < nx - 1 ? t + 1 : t)), f, 2);
+    }
+    {
+        const bool h = y > 0 && ty == 0;
+        from_dir<S>(slot_get<S>(slot, h, 3, h ? 2 * TY + tx : (y > 0 ? t - TX : t)), f, 3);
+    }
+    {
+        const bool h = y < ny - 1 && ty == TY - 1;
+        from_dir<S>(slot_get<S>(slot, h, 4, h ? 2 * TY + TX + tx : (y < ny - 1 ? t + TX : t)), f, 4);
+    }
+    from_dir<S>(d5, f, 5);
+    from_dir<S>(d6, f, 6);
+    FloatCell cell{f};
+    update_cell<2, false, false, false, true>(cell, x, y, z, ie, s2, 1.0f, true);
+    store_cell_evict_first<S>(s2, (z * ny + y) * s2.nxp + x, f);
+}
+
+template <class S>
+__device__ __forceinline__ void step2_body(const Step2Args &P)
+{
+    using namespace t2;
+    using L = T2L<S>;
+    extern __shared__ __align__(1024) unsigned char t2sm[];
+    __shared__ __align__(8) unsigned long long bars[2];
+    const StepArgs &s1 = P.s1, &s2 = P.s2;
+    const int nx = s1.nx, ny = s1.ny, nz = s1.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int t = threadIdx.x;
+    // z chunk of this block: planes [z0, z1); level n+1 runs over [pa, pb],
+    // one plane beyond the chunk on each side inside the grid (recomputed
+    // there, not recorded by the DFT)
+    const int z0 = blockIdx.z * P.zc, z1 = min(nz, z0 + P.zc);
+    const int pa = max(z0 - 1, 0), pb = min(z1, nz - 1);
+    const int nl1 = pb - pa + 1;  // >= 2 (nz >= 2)
+    const uint32_t bar0 = smem_u32(&bars[0]), buf0 = smem_u32(t2sm);
+    unsigned char *slots = t2sm + 2 * L::BUNDLE;
+
+    if (t == ISSUER) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == ISSUER) {
+        t2_issue<S>(P, buf0, bar0, x0, y0, pa, nz);
+        t2_issue<S>(P, buf0 + L::BUNDLE, bar0 + 8, x0, y0, pa + 1, nz);
+    }
+
+    // this thread's cell: a tile cell or an edge-halo cell (or none)
+    const bool tile = t < NT;
+    int x = -1, y = -1, hd = 0;
+    const int h = t - NT;
+    if (tile) {
+        x = x0 + t % TX;
+        y = y0 + t / TX;
+    } else if (h < NHALO) {
+        t2_halo(h, x0, y0, x, y, hd);
+    }
+    const bool live = x >= 0 && x < nx && y >= 0 && y < ny;
+    const int col = x - x0 + L::X0, row = y - y0 + 1;
+
+    // level n+1 groups of this column kept for the second step
+    DirVal<S> d0_prev{}, d5_prev{}, d5_pp{}, d6_cur{};
+    float ie_prev = 1.f;
+    // A copy that does not arrive within the bounded wait fails the block: it
+    // stops waiting, computing and issuing, but keeps every barrier, then
+    // reports the failure and waits (bounded) for its copies still in flight.
+    bool failed = false;  // uniform over the block after each barrier
+    int consumed = 0;     // bundles whose copies have landed
+    for (int j = 0; j < nl1; ++j) {
+        const int p = pa + j;
+        const unsigned char *buf = t2sm + (j & 1) * L::BUNDLE;
+        unsigned char *slot = slots + (p % 3) * L::SLOT;
+        bool bad = false;
+        if (!failed) {
+            bad = !mbar_wait_bounded(bar0 + 8 * (j & 1), (j >> 1) & 1);
+            if (!bad) consumed = j + 1;
+        }
+        DirVal<S> d0_cur{}, d5_cur{};
+        float ie_cur = 1.f;
+        if (live && !failed && !bad) {
+            float f[Planes<2>::Q];
+            bundle_cell<S>(buf, col, row, x, y, nx, ny, f);
+            const float ie = reinterpret_cast<const float *>(buf + L::EPS_OFF)[row * EPS_W + (x - x0 + EPS_X0)];
+            FloatCell cell{f};
+            update_cell<2, false, false, false, true>(cell, x, y, p, ie, s1, 1.0f, tile && p >= z0 && p < z1);
+            if (tile) {
+#pragma unroll
+                for (int d = 1; d <= 4; ++d) slot_put<S>(slot, false, d, t, to_dir<S>(f, d));
+                d0_cur = to_dir<S>(f, 0);
+                d5_cur = to_dir<S>(f, 5);
+                d6_cur = to_dir<S>(f, 6);
+                ie_cur = ie;
+            } else {
+                // the group pointing into the tile (constant indices keep f in registers)
+                const DirVal<S> v = hd == 1 ? to_dir<S>(f, 1)
+                                  : hd == 2 ? to_dir<S>(f, 2)
+                                  : hd == 3 ? to_dir<S>(f, 3)
+                                            : to_dir<S>(f, 4);
+                slot_put<S>(slot, true, 0, h, v);
+            }
+        }
+        // level n+1 of plane p is complete and its bundle buffer free
+        failed = __syncthreads_or(failed || bad) != 0;
+        if (!failed && t == ISSUER && j + 2 < nl1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            t2_issue<S>(P, buf0 + (j & 1) * L::BUNDLE, bar0 + 8 * (j & 1), x0, y0, p + 2, nz);
+        }
+        // level n+2 of plane p - 1 (p - 1 < z1 holds, since p <= pb <= z1);
+        // at p - 1 == 0 the +z pull clamps to the plane itself
+        if (!failed && tile && live && p - 1 >= z0)
+            t2_level2<S>(s2, slots + ((p - 1) % 3) * L::SLOT, t, x, y, p - 1, d0_prev,
+                         p - 1 == 0 ? d5_prev : d5_pp, d6_cur, ie_prev);
+        d5_pp = d5_prev;
+        d5_prev = d5_cur;
+        d0_prev = d0_cur;
+        ie_prev = ie_cur;
+    }
+    if (failed) {
+        if (t == ISSUER) {
+            atomicOr(s1.status, 1);
+            const int issued = min(consumed + 2, nl1);  // at most two bundles ahead of the last one consumed
+            for (int k = consumed; k < issued; ++k) mbar_wait_bounded(bar0 + 8 * (k & 1), (k >> 1) & 1);
+        }
+        return;
+    }
+    // the last plane of the grid pulls its -z group from itself (Eq. 4)
+    if (z1 == nz && tile && live)
+        t2_level2<S>(s2, slots + ((nz - 1) % 3) * L::SLOT, t, x, y, nz - 1, d0_prev, d5_pp, d6_cur, ie_prev);
+}
+
+// FP32: one block of 352 threads per SM (its shared memory), registers up to
+// 144; 16-bit: two blocks per SM, so 88 registers at most (the launch bound
+// for two blocks would cap them at 80 and spill).
+__global__ void __launch_bounds__(t2::THREADS, 1) step2_kernel_f32(const __grid_constant__ Step2Args P)
+{
+    step2_body<float>(P);
+}
+
+template <class S>
+__global__ void __maxnreg__(88) step2_kernel_16(const __grid_constant__ Step2Args P)
+{
+    step2_body<S>(P);
+}
+
+template <class S> struct Step2Kernel {
+    static constexpr auto fn = step2_kernel_16<S>;
+};
+template <> struct Step2Kernel<float> {
+    static constexpr auto fn = step2_kernel_f32;
+};
 
 // The incident line for both steps of a fused pair, in one block: the line
 // work of step n (DFT at n+1, line(n+2)), then of step n+1 (DFT at n+2,
 // line(n+3)).
 template <int MODE>
-__global__ void line2_kernel(const __grid_constant__ Step2Args P)
+__global__ void line2_kernel(const __grid_constant__ StepArgs s1, const __grid_constant__ StepArgs s2)
 {
-    for (int s = threadIdx.x; s < P.s1.n_line; s += blockDim.x) line_work<MODE>(P.s1, s);
+    for (int s = threadIdx.x; s < s1.n_line; s += blockDim.x) line_work<MODE>(s1, s);
     __syncthreads();
-    for (int s = threadIdx.x; s < P.s2.n_line; s += blockDim.x) line_work<MODE>(P.s2, s);
+    for (int s = threadIdx.x; s < s2.n_line; s += blockDim.x) line_work<MODE>(s2, s);
 }
 
 // Sums cnt staged steps of face fields into the FP64 DFT accumulators in step
@@ -1011,7 +1364,8 @@ cudaError_t launch_cell(StepArgs a, cudaStream_t s)
 {
     a.nblk_x = (a.nx + kBX - 1) / kBX;
     a.rows_per_block = rows_of<S>();
-    if ((long long)a.nblk_x * a.ny * a.nz / a.rows_per_block < kWaveBlocks) a.rows_per_block = 1;
+    if ((long long)a.nblk_x * a.ny * a.nz / a.rows_per_block < 7LL * std::max(1, sm_count()))
+        a.rows_per_block = 1;
     a.nblk_main = a.nblk_x * ((a.ny * a.nz + a.rows_per_block - 1) / a.rows_per_block);
     if (a.line_on && (a.n_line + kBX - 1) / kBX > a.nblk_main) return cudaErrorInvalidValue;
     if (REC && a.rec == nullptr) return cudaErrorInvalidValue;
@@ -1039,7 +1393,183 @@ int max_blocks_t()
     return n;
 }
 
+// ---- host side of the two-step pass
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once (the library links
+// the CUDA runtime statically and not the driver library).
+EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// A tiled tensor map without swizzle or interleave; out-of-range box cells
+// read zero (never used: pulls clamp inside the grid).
+bool encode_map(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
+                const cuuint64_t *strides, const cuuint32_t *box,
+                CUtensorMapL2promotion promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B)
+{
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return fn(m, dt, (cuuint32_t)rank, const_cast<void *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class S> constexpr int storage_slot() { return std::is_same<S, float>::value ? 0 : (std::is_same<S, __half>::value ? 1 : 2); }
+
+// Per device: the two-step kernels' shared-memory opt-in and their resident
+// blocks per SM (set up once, under a lock).
+std::mutex g_step2_mu;
+int g_step2_bps[kMaxDevices][3];
+
+template <class S>
+cudaError_t step2_setup(int &blocks_per_sm)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_step2_mu);
+    int &bps = g_step2_bps[dev][storage_slot<S>()];
+    if (bps == 0) {
+        e = cudaFuncSetAttribute(Step2Kernel<S>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T2L<S>::SMEM);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Step2Kernel<S>::fn, t2::THREADS, T2L<S>::SMEM);
+        if (e != cudaSuccess) return e;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        bps = n;
+    }
+    blocks_per_sm = bps;
+    return cudaSuccess;
+}
+
+// Whether two-step passes pay on this grid: the tiles times z chunks of at
+// least 16 planes fill one wave of resident blocks.  The grid must also hold
+// a whole box in x and y.
+template <class S>
+bool step2_worthwhile_t(int nx, int ny, int nz)
+{
+    if (nx < 64 || ny < 16 || nz < 2) return false;
+    int bps = 0;
+    if (step2_setup<S>(bps) != cudaSuccess) return false;
+    const long long tiles = (long long)((nx + t2::TX - 1) / t2::TX) * ((ny + t2::TY - 1) / t2::TY);
+    return tiles * std::max(1, nz / 16) >= (long long)std::max(1, sm_count()) * bps;
+}
+
+template <class S>
+cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+{
+    using L = T2L<S>;
+    if (s1.nx < 64 || s1.ny < 16 || s1.nz < 2 || s1.nxp % 32 || s1.P % 32) return cudaErrorInvalidValue;
+    int bps = 0;
+    cudaError_t e = step2_setup<S>(bps);
+    if (e != cudaSuccess) return e;
+    Step2Args P;
+    std::memset(&P, 0, sizeof P);
+    P.s1 = s1;
+    P.s2 = s2;
+    const char *f = static_cast<const char *>(s1.fin_q[0]);
+    const cuuint64_t nxp = s1.nxp, ny = s1.ny, nz = s1.nz, Pn = (cuuint64_t)s1.P;
+    bool ok;
+    if constexpr (sizeof(S) == 4) {
+        // 21 float2 groups, group g at 2 g P elements
+        const cuuint64_t dims[4] = {2 * nxp, ny, nz, 21}, str[3] = {8 * nxp, 8 * nxp * ny, 8 * Pn};
+        const cuuint32_t box[4] = {2 * L::W, t2::ROWS, 1, 3};
+        ok = encode_map(&P.map_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f, dims, str, box,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE);
+    } else {
+        // direction i: its quads at 6 i P elements, its pairs at (6 i + 4) P
+        const cuuint64_t dq[4] = {4 * nxp, ny, nz, 7}, sq[3] = {8 * nxp, 8 * nxp * ny, 12 * Pn};
+        const cuuint64_t dp[4] = {2 * nxp, ny, nz, 7}, sp[3] = {4 * nxp, 4 * nxp * ny, 12 * Pn};
+        const cuuint32_t bq[4] = {4 * L::W, t2::ROWS, 1, 1}, bp[4] = {2 * L::W, t2::ROWS, 1, 1};
+        ok = encode_map(&P.map_a, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, f, dq, sq, bq) &&
+             encode_map(&P.map_b, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, f + 8 * Pn, dp, sp, bp);
+    }
+    {
+        const cuuint64_t dims[3] = {nxp, ny, nz}, str[2] = {4 * nxp, 4 * nxp * ny};
+        const cuuint32_t box[3] = {t2::EPS_W, t2::ROWS, 1};
+        ok = ok && encode_map(&P.map_eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s1.inv_eps, dims, str, box);
+    }
+    if (!ok) return cudaErrorInvalidValue;
+    if (s1.line_on) {
+        line2_kernel<2><<<1, 512, 0, s>>>(P.s1, P.s2);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // z chunks: the chunk count that best fills whole waves of resident
+    // blocks, each chunk costing one extra plane of level n+1 (two at most)
+    const long long tiles = (long long)((s1.nx + t2::TX - 1) / t2::TX) * ((s1.ny + t2::TY - 1) / t2::TY);
+    const long long cap = (long long)std::max(1, sm_count()) * bps;
+    int zc = s1.nz;
+    double best = -1.0;
+    for (int k = 1; k <= s1.nz; ++k) {
+        const int c = (s1.nz + k - 1) / k;
+        if ((s1.nz + c - 1) / c != k) continue;
+        const long long blocks = tiles * k, waves = (blocks + cap - 1) / cap;
+        const double eff = (double)blocks / (double)(waves * cap) * (double)c / (c + 1.0);
+        if (eff > best + 1e-12) {
+            best = eff;
+            zc = c;
+        }
+        if (c < 8) break;
+    }
+    P.zc = zc;
+    dim3 grid((s1.nx + t2::TX - 1) / t2::TX, (s1.ny + t2::TY - 1) / t2::TY, (s1.nz + zc - 1) / zc);
+    if constexpr (L::CLUSTER_X > 1) {
+        // clusters of x-adjacent tiles (the grid padded to whole clusters;
+        // tiles beyond the grid compute nothing)
+        grid.x = (grid.x + L::CLUSTER_X - 1) / L::CLUSTER_X * L::CLUSTER_X;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(t2::THREADS);
+        cfg.dynamicSmemBytes = L::SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = L::CLUSTER_X;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, Step2Kernel<S>::fn, P);
+        if (e != cudaSuccess) return e;
+    } else {
+        Step2Kernel<S>::fn<<<grid, t2::THREADS, L::SMEM, s>>>(P);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int sm_count()
+{
+    static std::mutex mu;
+    static int cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
 
 // Failure-path check of the bounded grid barrier: one block waits for an
 // arrival that never comes, gives up after the bounded number of polls, sets
@@ -1092,46 +1622,24 @@ cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_step2(const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+cudaError_t launch_step2(int storage, const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
 {
-    if (s1.nz < 2 || s1.nx < 1 || s1.ny < 1) return cudaErrorInvalidValue;
-    // the shared-memory opt-in, once per device
-    static unsigned long long attr_set = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev >= 64 || !((attr_set >> dev) & 1ull)) {
-        e = cudaFuncSetAttribute(step2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT2Smem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) attr_set |= 1ull << dev;
+    switch (storage) {
+    case 0: return launch_step2_t<float>(s1, s2, s);
+    case 1: return launch_step2_t<__half>(s1, s2, s);
+    case 2: return launch_step2_t<__nv_bfloat16>(s1, s2, s);
+    default: return cudaErrorInvalidValue;
     }
-    Step2Args P;
-    P.s1 = s1;
-    P.s2 = s2;
-    if (s1.line_on) {
-        line2_kernel<2><<<1, 512, 0, s>>>(P);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    // z chunks: about two waves of blocks (2 per SM), chunks of at least 16
-    // planes (each costs two extra planes of level n+1)
-    const long long tiles = (long long)((s1.nx + kT2X - 1) / kT2X) * ((s1.ny + kT2Y - 1) / kT2Y);
-    int nzc = (int)std::min<long long>((4LL * 152 + tiles - 1) / tiles, std::max(1, s1.nz / 16));
-    nzc = std::max(1, nzc);
-    P.zc = (s1.nz + nzc - 1) / nzc;
-    nzc = (s1.nz + P.zc - 1) / P.zc;
-    const dim3 grid((s1.nx + kT2X - 1) / kT2X, (s1.ny + kT2Y - 1) / kT2Y, nzc);
-    step2_kernel<<<grid, kT2Threads, kT2Smem, s>>>(P);
-    return cudaGetLastError();
 }
 
-// Whether two-step passes pay on this grid: their blocks (tiles x z chunks)
-// must fill at least one wave of 2 blocks per SM.
-bool step2_worthwhile(int nx, int ny, int nz)
+bool step2_worthwhile(int storage, int nx, int ny, int nz)
 {
-    const long long tiles = (long long)((nx + kT2X - 1) / kT2X) * ((ny + kT2Y - 1) / kT2Y);
-    const long long chunks = std::max(1, nz / 16);
-    return nz >= 2 && tiles * chunks >= 2LL * 152;
+    switch (storage) {
+    case 0: return step2_worthwhile_t<float>(nx, ny, nz);
+    case 1: return step2_worthwhile_t<__half>(nx, ny, nz);
+    case 2: return step2_worthwhile_t<__nv_bfloat16>(nx, ny, nz);
+    default: return false;
+    }
 }
 
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s)

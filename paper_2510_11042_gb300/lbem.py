@@ -79,6 +79,7 @@ _SIGS = {
     "lbem_incident_amplitude": (_I32, [_P, ctypes.POINTER(ctypes.c_double)]),
     "lbem_set_far_field_precision": (_I32, [_P, _I32]),
     "lbem_set_step_fusion": (_I32, [_P, _I32]),
+    "lbem_get_step_fusion": (_I32, [_P, ctypes.POINTER(_I32)]),
     "lbem_get_populations": (_I32, [_P, _P, _I32]),
     "lbem_set_populations": (_I32, [_P, _P, _I32]),
     "lbem_fields": (_I32, [_P, _P, _P, _I32]),
@@ -247,6 +248,12 @@ def lbem_set_far_field_precision(h, precision):
 
 def lbem_set_step_fusion(h, steps_per_pass: int):
     _check(lib().lbem_set_step_fusion(h, int(steps_per_pass)), h)
+
+
+def lbem_get_step_fusion(h) -> int:
+    v = _I32()
+    _check(lib().lbem_get_step_fusion(h, ctypes.byref(v)), h)
+    return int(v.value)
 
 
 def lbem_incident_amplitude(h) -> float:
@@ -555,8 +562,13 @@ class Solver:
 
     def set_step_fusion(self, steps_per_pass):
         """2 (default): two steps per pass over the populations where supported
-        and worthwhile (3D FP32); 1: single steps."""
+        and worthwhile (3D grids without a mu_r map or closed-form source); 1:
+        single steps."""
         lbem_set_step_fusion(self.h, steps_per_pass)
+
+    def step_fusion(self):
+        """The steps per pass lbem_step takes as the handle is configured now."""
+        return lbem_get_step_fusion(self.h)
 
     def set_far_field_precision(self, precision):
         """"mixed" (FP32 contraction, FP64 sums above row chunks; default) or "fp64"."""
