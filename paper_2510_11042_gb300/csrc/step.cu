@@ -840,48 +840,57 @@ __global__ void line_init_kernel(const StepArgs a)
 // 16-bit storage level n+1 is rounded to the storage type before it is used,
 // so the result is bitwise that of two single steps.
 namespace t2 {
-constexpr int TX = 32, TY = 8;
-constexpr int NT = TX * TY;              // tile cells
-constexpr int NHALO = 2 * TY + 2 * TX;   // edge-halo cells
-constexpr int THREADS = 352;             // NT + NHALO, rounded up to whole warps
-constexpr int ISSUER = NT + NHALO;       // an idle lane of the last warp issues the copies
-constexpr int ROWS = TY + 2;             // box rows
+constexpr int TX = 32;                   // tile width (cells)
 constexpr int EPS_X0 = 4, EPS_W = 40;    // 1/eps_r box: 40 cells from x0 - 4 (16-byte aligned)
-constexpr int EPS_BYTES = ROWS * EPS_W * 4;
 __host__ __device__ constexpr int pad128(int b) { return (b + 127) / 128 * 128; }
 constexpr long long kWaitNs = 1000000000LL;  // a bounded wait gives up after 1 s
 }  // namespace t2
 
+// Tile geometry: 32 x TY cells, its edge halos, the threads (one per tile or
+// halo cell, whole warps) and the box rows (the tile's and one on each side).
+template <int TY_> struct T2Tile {
+    static constexpr int TX = t2::TX, TY = TY_;
+    static constexpr int NT = TX * TY;                       // tile cells
+    static constexpr int NHALO = 2 * TY + 2 * TX;            // edge-halo cells
+    static constexpr int THREADS = (NT + NHALO + 31) / 32 * 32;
+    // the thread that issues the copies: an idle lane of the last warp, else
+    // the last halo thread
+    static constexpr int ISSUER = NT + NHALO < THREADS ? NT + NHALO : THREADS - 1;
+    static constexpr int ROWS = TY + 2;
+    static constexpr int EPS_BYTES = ROWS * t2::EPS_W * 4;
+};
+
 // Shared-memory layout per storage type.  A bundle holds one box per
 // direction and 1/eps_r; a slot holds level n+1 of the +-x, +-y groups of the
 // tile cells and the one group of each halo cell.
-template <class S> struct T2L {
-    // 16-bit: per direction a quad (8 B) and a pair (4 B) per cell, boxes of
-    // 40 cells from x0 - 4 (a 4-byte pair's x coordinate must be a multiple of 4)
+template <class S> struct T2L : T2Tile<16> {
+    // 16-bit: tiles of 32 x 16 cells (one block of 608 threads per SM), per
+    // direction a quad (8 B) and a pair (4 B) per cell, boxes of 40 cells from
+    // x0 - 4 (a 4-byte pair's x coordinate must be a multiple of 4)
     static constexpr int X0 = 4, W = 40;
-    static constexpr int QUAD_BYTES = t2::ROWS * W * 8, PAIR_BYTES = t2::ROWS * W * 4;
+    static constexpr int QUAD_BYTES = ROWS * W * 8, PAIR_BYTES = ROWS * W * 4;
     static constexpr int PAIR_OFF = t2::pad128(QUAD_BYTES);
     static constexpr int DIR_BYTES = t2::pad128(PAIR_OFF + PAIR_BYTES);
     static constexpr int EPS_OFF = 7 * DIR_BYTES;
-    static constexpr int BUNDLE = t2::pad128(EPS_OFF + t2::EPS_BYTES);
-    static constexpr unsigned TX_BYTES = 7 * (QUAD_BYTES + PAIR_BYTES) + t2::EPS_BYTES;
-    static constexpr int S_TQ = 0, S_TP = 4 * t2::NT * 8, S_HQ = S_TP + 4 * t2::NT * 4,
-                         S_HP = S_HQ + t2::NHALO * 8;
-    static constexpr int SLOT = S_HP + t2::NHALO * 4;
+    static constexpr int BUNDLE = t2::pad128(EPS_OFF + EPS_BYTES);
+    static constexpr unsigned TX_BYTES = 7 * (QUAD_BYTES + PAIR_BYTES) + EPS_BYTES;
+    static constexpr int S_TQ = 0, S_TP = 4 * NT * 8, S_HQ = S_TP + 4 * NT * 4, S_HP = S_HQ + NHALO * 8;
+    static constexpr int SLOT = S_HP + NHALO * 4;
     static constexpr int SMEM = 2 * BUNDLE + 3 * SLOT;
-    static constexpr int MIN_BLOCKS = 2;
+    static constexpr int MIN_BLOCKS = 1;
     static constexpr int CLUSTER_X = 1;
 };
-template <> struct T2L<float> {
-    // FP32: per direction three float2 groups, boxes of 36 cells from x0 - 2
+template <> struct T2L<float> : T2Tile<8> {
+    // FP32: tiles of 32 x 8 cells (one block of 352 threads per SM), per
+    // direction three float2 groups, boxes of 36 cells from x0 - 2
     static constexpr int X0 = 2, W = 36;
-    static constexpr int GROUP_BYTES = t2::ROWS * W * 8;
+    static constexpr int GROUP_BYTES = ROWS * W * 8;
     static constexpr int DIR_BYTES = t2::pad128(3 * GROUP_BYTES);
     static constexpr int EPS_OFF = 7 * DIR_BYTES;
-    static constexpr int BUNDLE = t2::pad128(EPS_OFF + t2::EPS_BYTES);
-    static constexpr unsigned TX_BYTES = 7 * 3 * GROUP_BYTES + t2::EPS_BYTES;
-    static constexpr int S_TILE = 4 * 3 * t2::NT * 8;  // float2 [4 dirs][3][NT], then halo float2 [3][NHALO]
-    static constexpr int SLOT = S_TILE + 3 * t2::NHALO * 8;
+    static constexpr int BUNDLE = t2::pad128(EPS_OFF + EPS_BYTES);
+    static constexpr unsigned TX_BYTES = 7 * 3 * GROUP_BYTES + EPS_BYTES;
+    static constexpr int S_TILE = 4 * 3 * NT * 8;  // float2 [4 dirs][3][NT], then halo float2 [3][NHALO]
+    static constexpr int SLOT = S_TILE + 3 * NHALO * 8;
     static constexpr int SMEM = 2 * BUNDLE + 3 * SLOT;
     static constexpr int MIN_BLOCKS = 1;
     // launched in clusters of two x-adjacent tiles, with the boxes' L2 fetch
@@ -890,8 +899,8 @@ template <> struct T2L<float> {
     // without clusters and with 256-byte L2 promotion
     static constexpr int CLUSTER_X = 2;
 };
-static_assert(T2L<float>::SMEM <= 232448, "two-step FP32 shared memory");
-static_assert(2 * (T2L<__half>::SMEM + 1024) <= 233472, "two 16-bit two-step blocks per SM");
+static_assert(T2L<float>::SMEM <= 232448 - 1024, "two-step FP32 shared memory");
+static_assert(T2L<__half>::SMEM <= 232448 - 1024, "two-step 16-bit shared memory");
 
 // The six values of one direction of a cell in storage form.
 template <class S> struct DirVal { uint2 q; unsigned p; };   // 16-bit: quad + pair
@@ -974,12 +983,12 @@ __device__ __forceinline__ void slot_put(unsigned char *slot, bool halo, int d, 
 {
     using L = T2L<S>;
     if constexpr (sizeof(S) == 4) {
-        float2 *b = reinterpret_cast<float2 *>(slot) + (halo ? 4 * 3 * t2::NT + i : (d - 1) * 3 * t2::NT + i);
-        const int st = halo ? t2::NHALO : t2::NT;
+        float2 *b = reinterpret_cast<float2 *>(slot) + (halo ? 4 * 3 * L::NT + i : (d - 1) * 3 * L::NT + i);
+        const int st = halo ? L::NHALO : L::NT;
 #pragma unroll
         for (int k = 0; k < 3; ++k) b[k * st] = v.g[k];
     } else {
-        const int j = halo ? i : (d - 1) * t2::NT + i;
+        const int j = halo ? i : (d - 1) * L::NT + i;
         reinterpret_cast<uint2 *>(slot + (halo ? L::S_HQ : L::S_TQ))[j] = v.q;
         reinterpret_cast<unsigned *>(slot + (halo ? L::S_HP : L::S_TP))[j] = v.p;
     }
@@ -992,12 +1001,12 @@ __device__ __forceinline__ DirVal<S> slot_get(const unsigned char *slot, bool ha
     DirVal<S> v;
     if constexpr (sizeof(S) == 4) {
         const float2 *b =
-            reinterpret_cast<const float2 *>(slot) + (halo ? 4 * 3 * t2::NT + i : (d - 1) * 3 * t2::NT + i);
-        const int st = halo ? t2::NHALO : t2::NT;
+            reinterpret_cast<const float2 *>(slot) + (halo ? 4 * 3 * L::NT + i : (d - 1) * 3 * L::NT + i);
+        const int st = halo ? L::NHALO : L::NT;
 #pragma unroll
         for (int k = 0; k < 3; ++k) v.g[k] = b[k * st];
     } else {
-        const int j = halo ? i : (d - 1) * t2::NT + i;
+        const int j = halo ? i : (d - 1) * L::NT + i;
         v.q = reinterpret_cast<const uint2 *>(slot + (halo ? L::S_HQ : L::S_TQ))[j];
         v.p = reinterpret_cast<const unsigned *>(slot + (halo ? L::S_HP : L::S_TP))[j];
     }
@@ -1100,11 +1109,12 @@ __device__ __forceinline__ void t2_issue(const Step2Args &P, uint32_t dst, uint3
 }
 
 // Halo cell h of a tile at (x0, y0): its coordinates and the direction whose
-// group the tile pulls from it (h < 8: x0-1 (+x), < 16: x0+32 (-x), < 48:
-// y0-1 (+y), else y0+8 (-y)).
+// group the tile pulls from it (h < TY: x0-1 (+x), < 2 TY: x0+32 (-x),
+// < 2 TY + 32: y0-1 (+y), else y0+TY (-y)).
+template <class S>
 __device__ __forceinline__ void t2_halo(int h, int x0, int y0, int &x, int &y, int &dir)
 {
-    using namespace t2;
+    constexpr int TX = T2L<S>::TX, TY = T2L<S>::TY;
     if (h < TY) { x = x0 - 1; y = y0 + h; dir = 1; }
     else if (h < 2 * TY) { x = x0 + TX; y = y0 + h - TY; dir = 2; }
     else if (h < 2 * TY + TX) { x = x0 + h - 2 * TY; y = y0 - 1; dir = 3; }
@@ -1156,7 +1166,7 @@ template <class S>
 __device__ __forceinline__ void t2_level2(const StepArgs &s2, const unsigned char *slot, int t, int x, int y, int z,
                                           const DirVal<S> &d0, const DirVal<S> &d5, const DirVal<S> &d6, float ie)
 {
-    using namespace t2;
+    constexpr int TX = T2L<S>::TX, TY = T2L<S>::TY;
     const int nx = s2.nx, ny = s2.ny;
     const int tx = t % TX, ty = t / TX;
     float f[Planes<2>::Q];
@@ -1187,8 +1197,10 @@ __device__ __forceinline__ void t2_level2(const StepArgs &s2, const unsigned cha
 template <class S>
 __device__ __forceinline__ void step2_body(const Step2Args &P)
 {
-    using namespace t2;
     using L = T2L<S>;
+    constexpr int TX = L::TX, TY = L::TY, NT = L::NT, NHALO = L::NHALO, ISSUER = L::ISSUER;
+    using t2::EPS_W;
+    using t2::EPS_X0;
     extern __shared__ __align__(1024) unsigned char t2sm[];
     __shared__ __align__(8) unsigned long long bars[2];
     const StepArgs &s1 = P.s1, &s2 = P.s2;
@@ -1224,7 +1236,7 @@ __device__ __forceinline__ void step2_body(const Step2Args &P)
         x = x0 + t % TX;
         y = y0 + t / TX;
     } else if (h < NHALO) {
-        t2_halo(h, x0, y0, x, y, hd);
+        t2_halo<S>(h, x0, y0, x, y, hd);
     }
     const bool live = x >= 0 && x < nx && y >= 0 && y < ny;
     const int col = x - x0 + L::X0, row = y - y0 + 1;
@@ -1299,25 +1311,15 @@ __device__ __forceinline__ void step2_body(const Step2Args &P)
         t2_level2<S>(s2, slots + ((nz - 1) % 3) * L::SLOT, t, x, y, nz - 1, d0_prev, d5_pp, d6_cur, ie_prev);
 }
 
-// FP32: one block of 352 threads per SM (its shared memory), registers up to
-// 144; 16-bit: two blocks per SM, so 88 registers at most (the launch bound
-// for two blocks would cap them at 80 and spill).
-__global__ void __launch_bounds__(t2::THREADS, 1) step2_kernel_f32(const __grid_constant__ Step2Args P)
-{
-    step2_body<float>(P);
-}
-
+// One block per SM (its shared memory): FP32 352 threads, 16-bit 608.
 template <class S>
-__global__ void __maxnreg__(88) step2_kernel_16(const __grid_constant__ Step2Args P)
+__global__ void __launch_bounds__(T2L<S>::THREADS, T2L<S>::MIN_BLOCKS) step2_kernel(const __grid_constant__ Step2Args P)
 {
     step2_body<S>(P);
 }
 
 template <class S> struct Step2Kernel {
-    static constexpr auto fn = step2_kernel_16<S>;
-};
-template <> struct Step2Kernel<float> {
-    static constexpr auto fn = step2_kernel_f32;
+    static constexpr auto fn = step2_kernel<S>;
 };
 
 // The incident line for both steps of a fused pair, in one block: the line
@@ -1449,7 +1451,7 @@ cudaError_t step2_setup(int &blocks_per_sm)
         e = cudaFuncSetAttribute(Step2Kernel<S>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T2L<S>::SMEM);
         if (e != cudaSuccess) return e;
         int n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Step2Kernel<S>::fn, t2::THREADS, T2L<S>::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Step2Kernel<S>::fn, T2L<S>::THREADS, T2L<S>::SMEM);
         if (e != cudaSuccess) return e;
         if (n < 1) return cudaErrorInvalidConfiguration;
         bps = n;
@@ -1464,10 +1466,11 @@ cudaError_t step2_setup(int &blocks_per_sm)
 template <class S>
 bool step2_worthwhile_t(int nx, int ny, int nz)
 {
-    if (nx < 64 || ny < 16 || nz < 2) return false;
+    if (nx < 64 || ny < T2L<S>::ROWS || nz < 2) return false;
     int bps = 0;
     if (step2_setup<S>(bps) != cudaSuccess) return false;
-    const long long tiles = (long long)((nx + t2::TX - 1) / t2::TX) * ((ny + t2::TY - 1) / t2::TY);
+    using L = T2L<S>;
+    const long long tiles = (long long)((nx + L::TX - 1) / L::TX) * ((ny + L::TY - 1) / L::TY);
     return tiles * std::max(1, nz / 16) >= (long long)std::max(1, sm_count()) * bps;
 }
 
@@ -1475,7 +1478,7 @@ template <class S>
 cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
 {
     using L = T2L<S>;
-    if (s1.nx < 64 || s1.ny < 16 || s1.nz < 2 || s1.nxp % 32 || s1.P % 32) return cudaErrorInvalidValue;
+    if (s1.nx < 64 || s1.ny < L::ROWS || s1.nz < 2 || s1.nxp % 32 || s1.P % 32) return cudaErrorInvalidValue;
     int bps = 0;
     cudaError_t e = step2_setup<S>(bps);
     if (e != cudaSuccess) return e;
@@ -1489,20 +1492,20 @@ cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t 
     if constexpr (sizeof(S) == 4) {
         // 21 float2 groups, group g at 2 g P elements
         const cuuint64_t dims[4] = {2 * nxp, ny, nz, 21}, str[3] = {8 * nxp, 8 * nxp * ny, 8 * Pn};
-        const cuuint32_t box[4] = {2 * L::W, t2::ROWS, 1, 3};
+        const cuuint32_t box[4] = {2 * L::W, L::ROWS, 1, 3};
         ok = encode_map(&P.map_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f, dims, str, box,
                         CU_TENSOR_MAP_L2_PROMOTION_NONE);
     } else {
         // direction i: its quads at 6 i P elements, its pairs at (6 i + 4) P
         const cuuint64_t dq[4] = {4 * nxp, ny, nz, 7}, sq[3] = {8 * nxp, 8 * nxp * ny, 12 * Pn};
         const cuuint64_t dp[4] = {2 * nxp, ny, nz, 7}, sp[3] = {4 * nxp, 4 * nxp * ny, 12 * Pn};
-        const cuuint32_t bq[4] = {4 * L::W, t2::ROWS, 1, 1}, bp[4] = {2 * L::W, t2::ROWS, 1, 1};
+        const cuuint32_t bq[4] = {4 * L::W, L::ROWS, 1, 1}, bp[4] = {2 * L::W, L::ROWS, 1, 1};
         ok = encode_map(&P.map_a, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, f, dq, sq, bq) &&
              encode_map(&P.map_b, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, f + 8 * Pn, dp, sp, bp);
     }
     {
         const cuuint64_t dims[3] = {nxp, ny, nz}, str[2] = {4 * nxp, 4 * nxp * ny};
-        const cuuint32_t box[3] = {t2::EPS_W, t2::ROWS, 1};
+        const cuuint32_t box[3] = {t2::EPS_W, L::ROWS, 1};
         ok = ok && encode_map(&P.map_eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s1.inv_eps, dims, str, box);
     }
     if (!ok) return cudaErrorInvalidValue;
@@ -1513,7 +1516,7 @@ cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t 
     }
     // z chunks: the chunk count that best fills whole waves of resident
     // blocks, each chunk costing one extra plane of level n+1 (two at most)
-    const long long tiles = (long long)((s1.nx + t2::TX - 1) / t2::TX) * ((s1.ny + t2::TY - 1) / t2::TY);
+    const long long tiles = (long long)((s1.nx + L::TX - 1) / L::TX) * ((s1.ny + L::TY - 1) / L::TY);
     const long long cap = (long long)std::max(1, sm_count()) * bps;
     int zc = s1.nz;
     double best = -1.0;
@@ -1529,14 +1532,14 @@ cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t 
         if (c < 8) break;
     }
     P.zc = zc;
-    dim3 grid((s1.nx + t2::TX - 1) / t2::TX, (s1.ny + t2::TY - 1) / t2::TY, (s1.nz + zc - 1) / zc);
+    dim3 grid((s1.nx + L::TX - 1) / L::TX, (s1.ny + L::TY - 1) / L::TY, (s1.nz + zc - 1) / zc);
     if constexpr (L::CLUSTER_X > 1) {
         // clusters of x-adjacent tiles (the grid padded to whole clusters;
         // tiles beyond the grid compute nothing)
         grid.x = (grid.x + L::CLUSTER_X - 1) / L::CLUSTER_X * L::CLUSTER_X;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;
-        cfg.blockDim = dim3(t2::THREADS);
+        cfg.blockDim = dim3(L::THREADS);
         cfg.dynamicSmemBytes = L::SMEM;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
@@ -1549,7 +1552,7 @@ cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t 
         e = cudaLaunchKernelEx(&cfg, Step2Kernel<S>::fn, P);
         if (e != cudaSuccess) return e;
     } else {
-        Step2Kernel<S>::fn<<<grid, t2::THREADS, L::SMEM, s>>>(P);
+        Step2Kernel<S>::fn<<<grid, L::THREADS, L::SMEM, s>>>(P);
     }
     return cudaGetLastError();
 }
