@@ -111,12 +111,9 @@ __host__ __device__ inline long long pop_index(int mode, int elem_bytes, long lo
 // x*hi + x*lo evaluated with one rounding (FMA).  A plain x * fl(1/3) is biased
 // upwards (fl(1/3) > 1/3), which would make the collision grow D and B by
 // ~2e-8 per step; this form is unbiased.
-__device__ __forceinline__ float third(float x)
-{
-    constexpr float hi = 0.333333343267f;        // fl(1/3)
-    constexpr float lo = -9.934107481e-09f;      // 1/3 - fl(1/3)
-    return fmaf(x, hi, x * lo);
-}
+constexpr float kThirdHi = 0.333333343267f;     // fl(1/3)
+constexpr float kThirdLo = -9.934107481e-09f;   // 1/3 - fl(1/3)
+__device__ __forceinline__ float third(float x) { return fmaf(x, kThirdHi, x * kThirdLo); }
 
 // Direction i = 0..6: rest, +x, -x, +y, -y, +z, -z.
 __host__ __device__ constexpr int dir_axis(int i) { return i == 0 ? -1 : (i - 1) / 2; }

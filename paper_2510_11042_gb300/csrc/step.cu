@@ -318,10 +318,28 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
     using M = Mode<MODE>;
     constexpr int Q = PL::Q;
     float D[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
+    if constexpr (MODE == 2) {
+        // the same sums in packed pairs (D_x D_y), (D_z B_x), (B_y B_z): each
+        // lane adds in direction order, as the scalar loop below does
+        float2 p1 = make_float2(0.f, 0.f), p2 = p1, p3 = p1;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        if (PL::fam(q) == 0) D[PL::comp(q)] += f.get(q);
-        else B[PL::comp(q)] += f.get(q);
+        for (int i = 0; i < 7; ++i) {
+            p1 = __fadd2_rn(p1, make_float2(f.get(3 * i), f.get(3 * i + 1)));
+            p2 = __fadd2_rn(p2, make_float2(f.get(3 * i + 2), f.get(21 + 3 * i)));
+            p3 = __fadd2_rn(p3, make_float2(f.get(22 + 3 * i), f.get(23 + 3 * i)));
+        }
+        D[0] = p1.x;
+        D[1] = p1.y;
+        D[2] = p2.x;
+        B[0] = p2.y;
+        B[1] = p3.x;
+        B[2] = p3.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (PL::fam(q) == 0) D[PL::comp(q)] += f.get(q);
+            else B[PL::comp(q)] += f.get(q);
+        }
     }
     if (REC) {
         // total-field D of this step's pulled populations, for the adjoint's
@@ -338,11 +356,14 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
         for (int k = 0; k < PL::NE; ++k)
             a.rec[(long long)k * a.P + c] = D[M::ec(k)] * a.scale + Dinc[M::ec(k)];
     }
+    // E = D / eps_r and H = B / mu_r as products rounded on their own
+    // (__fmul_rn is never contracted into a later add, so every kernel that
+    // inlines this update rounds the fields the same way)
     float E[3], H[3], E3[3] = {0.f, 0.f, 0.f}, H3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int c3 = 0; c3 < 3; ++c3) {
-        E[c3] = D[c3] * inv_eps;
-        H[c3] = MU ? B[c3] * inv_mu : B[c3];
+        E[c3] = __fmul_rn(D[c3], inv_eps);
+        H[c3] = MU ? __fmul_rn(B[c3], inv_mu) : B[c3];
     }
 
     bool on_face = surface && a.dft_on && in_box(x, y, z, a.nt_lo, a.nt_hi);
@@ -420,6 +441,31 @@ __device__ __forceinline__ void update_cell(Cell &f, int x, int y, int z, float 
     const bool ana = ANA && in_box(x, y, z, a.tf_lo, a.tf_hi);
     if (!source && !ana && keep == 1.0f) {
         // most cells: plain collision, f* = 2 f_eq - f
+        if constexpr (MODE == 2) {
+            // in packed pairs (e_x e_y), (e_z h_x), (h_y h_z) per direction:
+            // 2 f_eq + (-1) f rounds once, as 2 f_eq - f does
+            const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                float eq[6];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    eq[k] = (i == 0) ? 2.f * (D[k] - E[k]) : E3[k] - cross_c(i, H3, k);
+                    eq[3 + k] = (i == 0) ? (MU ? 2.f * (B[k] - H[k]) : 0.f) : H3[k] + cross_c(i, E3, k);
+                }
+                const int qe = 3 * i, qh = 21 + 3 * i;
+                const float2 r0 = __ffma2_rn(make_float2(f.get(qe), f.get(qe + 1)), m1, make_float2(eq[0], eq[1]));
+                const float2 r1 = __ffma2_rn(make_float2(f.get(qe + 2), f.get(qh)), m1, make_float2(eq[2], eq[3]));
+                const float2 r2 = __ffma2_rn(make_float2(f.get(qh + 1), f.get(qh + 2)), m1, make_float2(eq[4], eq[5]));
+                f.set(qe, r0.x);
+                f.set(qe + 1, r0.y);
+                f.set(qe + 2, r1.x);
+                f.set(qh, r1.y);
+                f.set(qh + 1, r2.x);
+                f.set(qh + 2, r2.y);
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int i = PL::dir(q), ac = PL::comp(q);
