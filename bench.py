@@ -171,14 +171,6 @@ def max_over_ranks(t_ms: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def two_step_applies(nx: int, ny: int, nz: int) -> bool:
-    """Whether lbem_step takes two-step passes on a 3D FP32 grid: tiles of
-    32 x 8 cells times z chunks of at least 16 planes fill one wave of blocks
-    (2 per SM on 152 SMs), as the library decides."""
-    tiles = -(-nx // 32) * -(-ny // 8)
-    return nz >= 2 and tiles * max(1, nz // 16) >= 2 * 152
-
-
 def job_mlups(cells: int, updates_per_step: int, steps: int, world: int, t_ms: float) -> float:
     """Whole-job throughput: every rank advances its own replica of the
     workload, so the job updates cells x updates x steps x world sites."""
@@ -218,6 +210,7 @@ def run_gpu(args, rank, world, local_rank):
         solver.inject(prob.wave)
         h = solver.h
         stream = solver.stream
+        steps_per_pass = solver.step_fusion()   # the kernel lbem_step takes, as the library reports it
 
         def bench_step(ev_pair=None):
             lbem.lbem_set_dft_window(h, solver.time + 1, 1)
@@ -255,6 +248,7 @@ def run_gpu(args, rank, world, local_rank):
         step_kernel_ms = sum(a.elapsed_time(b) for a, b in evs) / (K * T)
         s2 = s2.reshape(3, 181).T
         out = dict(total_ms=total_ms, ms_per_step=total_ms / K, kernel_ms=step_kernel_ms,
+                   steps_per_pass=steps_per_pass,
                    launches=launches, clocks=clocks, periods=solver.time // T,
                    mie_nrms=[nrms(s2[:, j], ref[:, j]) for j in range(3)],
                    incident=lbem.lbem_incident_amplitude(h))
@@ -308,7 +302,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return
     hbm, peak_kind = peaks()
-    two_step = two_step_applies(nx, ny, nz)
+    two_step = main["steps_per_pass"] == 2
     value = job_mlups(cells, T, K, world, t_main)
     bc = b_cell("3d", "f32")
     achieved = bc * cells / (main["kernel_ms"] / 1e3) / 1e9
@@ -317,6 +311,7 @@ def run_gpu(args, rank, world, local_rank):
     storage_modes = {"f32": {"mlups": round(value / world, 1),
                              "kernel_ms": round(main["kernel_ms"], 4),
                              "hbm_frac": round(achieved / hbm, 4),
+                             "steps_per_pass": main["steps_per_pass"],
                              "mie_nrms_phi_0_45_90": [round(v, 5) for v in main["mie_nrms"]]}}
     for st, r in secondary.items():
         bcs = b_cell("3d", st)
@@ -325,9 +320,8 @@ def run_gpu(args, rank, world, local_rank):
                              "kernel_ms": round(r["kernel_ms"], 4),
                              "hbm_frac": round(ach / hbm, 4),
                              "speedup_vs_f32": round(main["kernel_ms"] / r["kernel_ms"], 3),
-                             "speedup_vs_f32_single_step": (
-                                 round(variants_3d["single_step"]["kernel_ms"] / r["kernel_ms"], 3)
-                                 if variants_3d else None),
+                             "mlups_vs_f32": round(cells * T * K / (r["total_ms"] / 1e3) / 1e6 / (value / world), 3),
+                             "steps_per_pass": r["steps_per_pass"],
                              "mie_nrms_phi_0_45_90": [round(v, 5) for v in r["mie_nrms"]]}
     line = {
         "metric": METRIC,
@@ -407,16 +401,22 @@ def run_batched(dev, count=32, seed=20251011):
     import torch
     from paper_2510_11042_gb300 import lbem
     out = {}
+    mie = None
+    if (count, seed) == (32, 20251011):
+        mie = np.loadtxt(os.path.join(GOLDEN, "mie_batch_cylinders_seed20251011.txt"))[:, 1:]
     for label, probs in (("cylinders_256_1024", W.batched_problems(count, seed)),
                          ("small_64_192", small_problems())):
-        out[label] = _batch_vs_sequential(dev, probs)
+        out[label] = _batch_vs_sequential(dev, probs, mie if label == "cylinders_256_1024" else None)
     out["cylinders_256_1024"]["workload"] = (f"{count} cylinders, seed {seed}, N 256-1024, "
                                              "40 periods each, FP32, EZ")
     out["small_64_192"]["workload"] = "64 cylinders, seed 7, N 64-192, 300 steps each, FP32, EZ"
     return out
 
 
-def _batch_vs_sequential(dev, probs):
+def _batch_vs_sequential(dev, probs, mie=None):
+    """Persistent batched run against one problem after another; with mie
+    ([181][problem] Lorenz-Mie TM |S|^2), also each batched problem's far
+    field at theta = 0..180 deg against it (Eq. 13)."""
     import torch
     from paper_2510_11042_gb300 import lbem
     work = sum(p.shape[0] * p.shape[1] * p.steps for p in probs)
@@ -439,6 +439,10 @@ def _batch_vs_sequential(dev, probs):
     t_batch = time.perf_counter() - t0
     bps, rpi, _, split = batch.config()
     batch.close()
+    mie_nrms = None
+    if mie is not None:
+        th = np.radians(np.arange(181.0))
+        mie_nrms = [round(nrms(s.far_field(th), mie[:, j]), 5) for j, s in enumerate(sol)]
     for s in sol:
         s.close()
     del sol
@@ -454,10 +458,16 @@ def _batch_vs_sequential(dev, probs):
         s.close()
     del sol
     torch.cuda.empty_cache()
-    return {"cell_updates": work, "persistent_mlups": round(work / t_batch / 1e6, 1),
-            "sequential_mlups": round(work / t_seq / 1e6, 1),
-            "speedup": round(t_seq / t_batch, 3),
-            "autotuned": {"blocks_per_sm": bps, "rows_per_item": rpi, "split": split}}
+    out = {"cell_updates": work, "persistent_mlups": round(work / t_batch / 1e6, 1),
+           "sequential_mlups": round(work / t_seq / 1e6, 1),
+           "speedup": round(t_seq / t_batch, 3),
+           "autotuned": {"blocks_per_sm": bps, "rows_per_item": rpi, "split": split}}
+    if mie_nrms is not None:
+        out["mie_nrms_per_problem"] = mie_nrms
+        out["mie_nrms_max"] = max(mie_nrms)
+        out["mie_nrms_median"] = float(np.median(mie_nrms))
+        out["mie_reference"] = "tests/golden/mie_batch_cylinders_seed20251011.txt (TM, theta 0..180 deg)"
+    return out
 
 
 # ------------------------------------------------------------------ 2D bandwidth probe

@@ -371,9 +371,15 @@ int32_t lbem_adjoint_timing(lbem_handle h, double *replay_ms, double *backward_m
  * the library holds until the process exits; n > LBEM_NOALLOC_MAX_ANGLES is
  * rejected with LBEM_ERR_ARG (split larger angle sets over several calls).
  * The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before any stream
- * capture.  All calls share the array, so calls whose work overlaps on the GPU
- * (different streams, or threads) race and must be serialised by the caller.
+ * device, with the device current) and keeps it for the process: it assumes
+ * the CUDA runtime's primary context of the device and no cudaDeviceReset
+ * afterwards.  Make that first call before any stream capture.  All calls
+ * share the array, so calls whose work overlaps on the GPU (different streams,
+ * or threads) race and must be serialised by the caller.  Every pointer must
+ * be device (or managed) memory of the current device, and the caller sizes
+ * them: dft_dev as lbem_get_dft lays out desc's NTFF box, theta_dev, phi_dev
+ * and s2_dev n doubles, amp_dev 12 n; a host pointer or one of another device
+ * is rejected with LBEM_ERR_ARG, sizes cannot be checked here.
  * Asynchronous on cuda_stream (NULL: legacy default stream); errors are
  * reported by the return code and lbem_last_error(NULL). */
 #define LBEM_NOALLOC_MAX_ANGLES 1024

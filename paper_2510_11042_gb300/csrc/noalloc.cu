@@ -25,7 +25,6 @@ using namespace lbem;
 namespace {
 
 constexpr int kNoAllocChunks = 16;            // face-cell chunks per angle
-constexpr int kMaxDevices = 64;
 
 // Partial sums [angle][chunk][12]: 1024 x 16 x 12 doubles = 1.5 MB per device.
 __device__ __align__(256) double g_far_field_scratch[LBEM_NOALLOC_MAX_ANGLES * kNoAllocChunks * 12];
@@ -103,6 +102,21 @@ int arg_error(const char *msg)
     return LBEM_ERR_ARG;
 }
 
+// Whether p is device (or managed) memory of the current device: a host
+// pointer handed to the kernels would fault, or on a system where the GPU can
+// read host memory silently be used.  The query allocates nothing.
+bool on_current_device(const void *p)
+{
+    if (!p) return true;
+    int dev = 0;
+    cudaPointerAttributes at;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of the query
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 }  // namespace
 
 extern "C" int32_t lbem_far_field_noalloc(const lbem_ntff_desc *d, const double *dft_dev,
@@ -126,6 +140,9 @@ extern "C" int32_t lbem_far_field_noalloc(const lbem_ntff_desc *d, const double 
     if (n == 0) return LBEM_OK;
     if (!dft_dev || !theta_dev || !s2_dev || (d->mode == 2 && !phi_dev))
         return arg_error("lbem_far_field_noalloc: NULL input or output");
+    if (!on_current_device(dft_dev) || !on_current_device(theta_dev) || !on_current_device(s2_dev) ||
+        (d->mode == 2 && !on_current_device(phi_dev)) || !on_current_device(amp_dev))
+        return arg_error("lbem_far_field_noalloc: inputs and outputs must be device memory of the current device");
 
     double *scratch = nullptr;
     cudaError_t e = scratch_of_current_device(&scratch);

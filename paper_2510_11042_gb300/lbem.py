@@ -327,15 +327,55 @@ def lbem_get_storage_scale(h) -> float:
     return v.value
 
 
+def ntff_dft_doubles(desc: NtffDesc) -> int:
+    """Doubles of the face-phasor layout of lbem_get_dft for desc's NTFF box:
+    per face (x faces, y faces, then z faces in 3D; low side first) NC
+    components x (re, im) x nu x nv, NC = 3 in 2D and 6 in 3D."""
+    n3 = (desc.nx, desc.ny, desc.nz)
+    nc = 6 if desc.mode == MODE["3d"] else 3
+    total = 0
+    for ax in range(3):
+        if n3[ax] <= 1:
+            continue
+        ua, va = (1 if ax == 2 else 2), (1 if ax == 0 else 0)
+        nu = desc.ntff_hi[ua] - desc.ntff_lo[ua] + 1
+        nv = desc.ntff_hi[va] - desc.ntff_lo[va] + 1
+        total += 2 * nc * 2 * nu * nv
+    return total
+
+
+def _device_f64(name, t, n, exact=False):
+    """A contiguous FP64 CUDA tensor of the current device holding at least
+    (exactly, with exact) n values, else LbemError(LBEM_ERR_ARG): the C entry
+    point cannot see sizes, and a short or host buffer would make its kernels
+    read or write out of bounds."""
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+          and t.device.index == torch.cuda.current_device())
+    if not ok:
+        raise LbemError(LBEM_ERR_ARG, f"{name}: a contiguous float64 CUDA tensor on the current device is required")
+    if (t.numel() != n) if exact else (t.numel() < n):
+        raise LbemError(LBEM_ERR_ARG, f"{name}: {t.numel()} values, {'exactly ' if exact else ''}{n} needed")
+
+
 def lbem_far_field_noalloc(desc: NtffDesc, dft_dev, theta_dev, phi_dev, s2_dev, amp_dev=None,
                            stream=None):
-    """Device tensors in and out (torch CUDA tensors); allocates nothing."""
+    """Device tensors in and out (torch CUDA tensors, FP64, on the current
+    device); allocates nothing.  Checks every buffer against the sizes desc and
+    the angle count imply before the call."""
+    n = theta_dev.numel() if hasattr(theta_dev, "numel") else len(theta_dev)
+    _device_f64("theta", theta_dev, n)
+    _device_f64("s2", s2_dev, n)
+    if desc.mode == MODE["3d"] or phi_dev is not None:
+        _device_f64("phi", phi_dev, n)
+    if amp_dev is not None:
+        _device_f64("amp", amp_dev, 12 * n)
+    _device_f64("dft", dft_dev, ntff_dft_doubles(desc), exact=True)
     dp, _ = _ptr(dft_dev)
     tp, _ = _ptr(theta_dev)
     pp, _ = _ptr(phi_dev)
     sp, _ = _ptr(s2_dev)
     ap, _ = _ptr(amp_dev)
-    n = theta_dev.numel() if hasattr(theta_dev, "numel") else len(theta_dev)
     _check(lib().lbem_far_field_noalloc(ctypes.byref(desc), dp, tp, pp, int(n), sp, ap, stream))
 
 

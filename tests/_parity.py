@@ -103,3 +103,31 @@ def angles(mode):
         ph3 = np.concatenate([np.zeros(181), np.full(181, math.pi / 4), np.full(181, math.pi / 2)])
         return th3, ph3
     return th, None
+
+
+def oracle_far_field_of(job):
+    """|S|^2 of an FP64 oracle run of `problem` with permittivity `eps`
+    (a worker of a spawned process pool: job = (problem, eps, theta, threads))."""
+    import dataclasses
+    from oracle import lb, ntff
+    problem, eps, theta, threads = job
+    lb.set_threads(threads)
+    r = lb.Run(dataclasses.replace(problem, eps=eps)).run()
+    w = problem.wave
+    k = 2 * math.pi / w.wavelength
+    return ntff.far_field(r.phasors(), w.ntff_lo, w.ntff_hi, k, w.center, r.incident_amplitude(),
+                          problem.mode, theta)
+
+
+def oracle_far_fields(problem, eps_list, theta):
+    """oracle_far_field_of for several permittivity maps, in a pool of spawned
+    processes (never forked after CUDA is up) that splits the host's cores."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    cores = os.cpu_count() or 1
+    workers = max(1, min(len(eps_list), cores // 4))
+    threads = max(1, cores // workers)
+    jobs = [(problem, e, theta, threads) for e in eps_list]
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(oracle_far_field_of, jobs))

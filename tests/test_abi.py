@@ -64,3 +64,21 @@ def test_create_without_usable_device_fails_loudly():
     g = lbem.grid_desc(8, 8, 1, "ez", "f32", 0)
     with pytest.raises(lbem.LbemError):
         lbem.lbem_create(g, np.ones((1, 8, 8), np.float32))
+
+
+def test_noalloc_wrapper_sizes_and_refusals_on_host():
+    """The no-alloc far field's binding sizes the DFT buffer from the NTFF box
+    (faces of nu x nv cells, NC components, re and im) and refuses host arrays
+    before any library call, so no kernel can be handed a host pointer."""
+    import numpy as np
+    pytest.importorskip("torch")
+    # 2D box of 24 x 24 cells: 4 faces of 24 cells, 3 components
+    d2 = lbem.NtffDesc(0, 32, 32, 1, (4, 4, 0), (27, 27, 0), 8.0, (15.5, 15.5, 0.0), 1.0)
+    assert lbem.ntff_dft_doubles(d2) == 4 * 24 * 3 * 2
+    # 3D box of 8 x 6 x 5 cells: x faces 5 x 6, y faces 5 x 8, z faces 6 x 8; 6 components
+    d3 = lbem.NtffDesc(2, 12, 12, 12, (2, 3, 4), (9, 8, 8), 8.0, (5.5, 5.5, 5.5), 1.0)
+    assert lbem.ntff_dft_doubles(d3) == 2 * (5 * 6 + 5 * 8 + 6 * 8) * 6 * 2
+    th = np.zeros(4)
+    with pytest.raises(lbem.LbemError) as ei:
+        lbem.lbem_far_field_noalloc(d2, np.zeros(lbem.ntff_dft_doubles(d2)), th, None, np.zeros(4))
+    assert ei.value.code == lbem.LBEM_ERR_ARG

@@ -25,6 +25,11 @@ pytestmark = pytest.mark.gpu
 
 J_TOL = 1e-5
 G_TOL = 2e-4
+# Per-cell bound where |fd| > 1e-2 max |g|: the FP32 gradient's error measured
+# against the FP64 oracle is within 2e-6 of max |g| (the sum over every step of
+# forward-adjoint products cancels heavily), i.e. within 2e-4 of such an |fd|;
+# the FP64 central differences add ~(1e-4)^2 truncation.  Bar at 10x that.
+FD_CELL_TOL = 2e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -160,8 +165,10 @@ def test_adjoint_state_errors():
 def test_hexagon_gradient_vs_finite_differences():
     """512 x 512 hexagon, 4000 steps, K = 200: dJ/deps_r of |S(theta)|^2 at 0, 45
     and 90 degrees against central differences (h = 1e-4 eps_r) of FP64
-    oracle runs on seeded design cells (LBEM_FD_CELLS, default 2)."""
-    from oracle import lb, ntff
+    oracle runs on 16 seeded random design cells (LBEM_FD_CELLS overrides the
+    count).  Each cell is checked against the largest gradient entry, and
+    where |fd| exceeds 1e-2 of that also against |fd| itself."""
+    from _parity import oracle_far_fields
     p = W.adjoint_problem()
     theta = np.array(p.meta["angles"])
     from paper_2510_11042_gb300 import lbem
@@ -175,29 +182,31 @@ def test_hexagon_gradient_vs_finite_differences():
         wk[k] = 1.0
         J, g = s.adjoint(theta, None, wk)
         grads.append((J, g.cpu().numpy().astype(np.float64)))
-    ncells = int(os.environ.get("LBEM_FD_CELLS", "2"))
+    s.close()
+    ncells = int(os.environ.get("LBEM_FD_CELLS", "16"))
     rng = np.random.default_rng(7)
     c0, d = p.meta["design_lo"], p.meta["design"]
     cells = [(0, int(c0 + rng.integers(d)), int(c0 + rng.integers(d))) for _ in range(ncells)]
-    k = 2 * math.pi / p.wave.wavelength
-
-    def s2_oracle(eps):
-        r = lb.Run(dataclasses.replace(p, eps=eps)).run()
-        return ntff.far_field(r.phasors(), p.wave.ntff_lo, p.wave.ntff_hi, k, p.wave.center,
-                              r.incident_amplitude(), "ez", theta)
 
     base = np.asarray(p.eps, np.float64)
-    s2o = s2_oracle(base)
-    for kk in range(3):
-        assert abs(grads[kk][0] - s2o[kk]) <= J_TOL * s2o[kk], (kk, grads[kk][0], s2o[kk])
+    maps, steps = [base], []
     for cell in cells:
         h = 1e-4 * base[cell]
         ep = base.copy(); ep[cell] += h
         em = base.copy(); em[cell] -= h
-        fd = (s2_oracle(ep) - s2_oracle(em)) / (2 * h)
+        maps += [ep, em]
+        steps.append(h)
+    s2s = oracle_far_fields(p, maps, theta)
+    s2o = s2s[0]
+    for kk in range(3):
+        assert abs(grads[kk][0] - s2o[kk]) <= J_TOL * s2o[kk], (kk, grads[kk][0], s2o[kk])
+    for c, (cell, h) in enumerate(zip(cells, steps)):
+        fd = (s2s[1 + 2 * c] - s2s[2 + 2 * c]) / (2 * h)
         for kk in range(3):
             g = grads[kk][1]
             gmax = np.max(np.abs(g))
             print(f"cell {cell} theta {math.degrees(theta[kk]):.0f}: adjoint {g[cell]:.6e} "
                   f"fd {fd[kk]:.6e} (max |g| {gmax:.3e})")
             assert abs(g[cell] - fd[kk]) <= G_TOL * gmax + 1e-3 * abs(fd[kk])
+            if abs(fd[kk]) > 1e-2 * gmax:
+                assert abs(g[cell] - fd[kk]) <= FD_CELL_TOL * abs(fd[kk]), (cell, kk, g[cell], fd[kk])

@@ -78,6 +78,30 @@ def test_random_state_parity_fp32(mode, shape):
     assert s.incident_amplitude() == pytest.approx(r.incident_amplitude(), rel=TOL)
 
 
+@pytest.mark.parametrize("mode,shape,steps", [("ez", (96, 80, 1), 240), ("hz", (96, 80, 1), 240),
+                                              ("3d", (40, 36, 44), 216)])
+def test_random_media_driven_phasor_parity_fp32(mode, shape, steps):
+    """Random eps_r in [1, 6] inside the box, driven from rest by the plane wave
+    (lambda = 8, T = 24) until the scattered wave has crossed the NTFF faces;
+    the DFT over the last two periods then carries the drive's signal, and the
+    phasors match the oracle's in plain relative L2, as do |S|^2."""
+    p = random_problem(mode, shape, steps=steps)
+    p = dataclasses.replace(p, dft_periods=2)
+    s = gpu_solver(p)
+    r = oracle_run(p)
+    assert rel_l2(s.populations(), oracle_to_planes(r.main.f, mode, shape)) <= TOL
+    from paper_2510_11042_gb300 import lbem
+    faces = lbem.dft_faces(s.dft(), mode, shape, p.wave.ntff_lo, p.wave.ntff_hi)
+    ref = oracle_faces(r.phasors(), mode, p.wave.ntff_lo, p.wave.ntff_hi)
+    got = np.concatenate([f["data"].ravel() for f in faces])
+    exp = np.concatenate([f.ravel() for f in ref])
+    assert got.shape == exp.shape and np.linalg.norm(exp) > 0
+    err_x = rel_l2(got, exp)
+    assert err_x <= TOL, err_x
+    th, ph = angles(mode)
+    assert rel_l2(s.far_field(th, ph), _far_field_oracle(r, p)) <= TOL
+
+
 def _far_field_oracle(r, p):
     from oracle import ntff
     k = 2 * math.pi / p.wave.wavelength
