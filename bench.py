@@ -472,32 +472,41 @@ def _batch_vs_sequential(dev, probs, mie=None):
 
 # ------------------------------------------------------------------ 2D bandwidth probe
 def run_probe_2d(dev, n=4096, updates=60):
-    """Step-kernel bandwidth of the 2D EZ path on a grid well above L2
-    (4096^2 x 21 populations, 2.8 GB in FP32): a cylinder of the cylinder
-    workload's proportions, CUDA events around `updates` lattice updates."""
+    """Step throughput of the 2D EZ path on a grid well above L2 (4096^2 x 21
+    populations, 2.8 GB in FP32): a cylinder of the cylinder workload's
+    proportions, CUDA events around `updates` lattice updates, with the pass
+    lbem_step takes by default (two updates per pass where the library
+    reports it) and with single steps.  hbm_frac is the byte model
+    (B_cell per update) over the time per update."""
     import torch
     from paper_2510_11042_gb300 import lbem
     p = W.cylinder_problem(n=n, x=5.0, wavelength=40.0, eps_in=2.25, w=20, mode="ez", periods=1)
     hbm, _ = peaks()
     out = {"workload": f"cylinder {n}x{n} EZ, lambda 40, W 20", "cells": n * n}
-    for st in ("f32", "f16"):
-        s = lbem.Solver(p.shape, p.eps, "ez", st, p.absorber_width, p.sigma_max, device=dev)
-        s.inject(p.wave)
-        s.step(10)
-        torch.cuda.synchronize(dev)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(s.stream)
-        s.step(updates)
-        ev[1].record(s.stream)
-        torch.cuda.synchronize(dev)
-        ms = ev[0].elapsed_time(ev[1]) / updates
-        bc = b_cell("ez", st)
-        gbs = bc * n * n / (ms / 1e3) / 1e9
-        out[st] = {"kernel_ms": round(ms, 4), "mlups": round(n * n / (ms / 1e3) / 1e6, 1),
-                   "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
-        s.close()
-        del s
-        torch.cuda.empty_cache()
+    for st in ("f32", "f16", "bf16"):
+        rec = {}
+        for fuse in (2, 1):
+            s = lbem.Solver(p.shape, p.eps, "ez", st, p.absorber_width, p.sigma_max, device=dev)
+            s.set_step_fusion(fuse)
+            s.inject(p.wave)
+            s.step(10)
+            torch.cuda.synchronize(dev)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(s.stream)
+            s.step(updates)
+            ev[1].record(s.stream)
+            torch.cuda.synchronize(dev)
+            ms = ev[0].elapsed_time(ev[1]) / updates
+            bc = b_cell("ez", st)
+            gbs = bc * n * n / (ms / 1e3) / 1e9
+            rec[fuse] = {"kernel_ms": round(ms, 4), "mlups": round(n * n / (ms / 1e3) / 1e6, 1),
+                         "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                         "steps_per_pass": s.step_fusion()}
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+        out[st] = dict(rec[2], single_step=rec[1], speedup_vs_single_step=round(rec[1]["kernel_ms"] /
+                                                                                rec[2]["kernel_ms"], 3))
     return out
 
 
@@ -745,8 +754,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-updates", type=float, default=2)
-    ap.add_argument("--section", default="all", choices=["all", "adjoint_probe"],
-                    help="adjoint_probe: only the above-L2 adjoint measurement (profiling)")
+    ap.add_argument("--section", default="all", choices=["all", "adjoint_probe", "probe_2d"],
+                    help="adjoint_probe / probe_2d: only that measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -756,11 +765,13 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.section == "adjoint_probe":
+    if args.section in ("adjoint_probe", "probe_2d"):
         import torch
         from paper_2510_11042_gb300 import build as lib_build
         lib_build.build()
-        print(json.dumps(_adjoint_probe_3d(torch.device("cuda", local_rank))), flush=True)
+        dev = torch.device("cuda", local_rank)
+        fn = _adjoint_probe_3d if args.section == "adjoint_probe" else run_probe_2d
+        print(json.dumps(fn(dev)), flush=True)
         return
     if world > 1:
         import torch

@@ -1379,6 +1379,310 @@ __global__ void line2_kernel(const __grid_constant__ StepArgs s1, const __grid_c
     for (int s = threadIdx.x; s < s2.n_line; s += blockDim.x) line_work<MODE>(s2, s);
 }
 
+// ---------------------------------------------------------------------------
+// Two steps per pass over HBM in 2D (EZ and HZ; FP32, FP16 and BF16
+// storage): the temporal blocking above with y as the marching axis.  A
+// block owns a strip of 128 cells along x and marches along y through a chunk
+// of rows; each strip thread keeps one x column.  For every row r:
+//   * level n+1 of the strip and of its two edge-halo cells (x0-1 and x0+128)
+//     is computed from a bundle of level-n rows in shared memory: the rest,
+//     +-x, +-z groups of row r, the +y group of row r-1 and the -y group of
+//     row r+1 (each row index clamped to the grid, Eq. 4), boxes from 4 (FP32)
+//     or 8 (16-bit) cells left of the strip to as many right of it, and
+//     1/eps_r of row r; the +-z pulls of a 2D grid read the cell itself;
+//   * level n+2 of row r-1 is computed from level n+1: the +-x groups from
+//     shared memory (strip and halo cells), the rest, +-z groups of row r-1,
+//     the +y group of row r-2 and the -y group of row r from the column's own
+//     registers, and written to HBM.
+// One elected thread keeps the copies of up to three rows ahead in flight
+// (four bundle buffers, each with its mbarrier).  Level n+1 of the +-x groups
+// lives in three rotating slots, so one block barrier per row orders
+// everything.  A chunk recomputes level n+1 of one row on each side (not
+// recorded by the DFT).  Every update is update_cell; 16-bit storage rounds
+// level n+1 to the storage type, so the result is bitwise that of two single
+// steps.
+namespace t2d {
+constexpr int TXS = 128;                 // strip width (cells)
+constexpr int THREADS = 160;             // 128 strip cells, 2 halo cells, idle lanes
+constexpr int HALO = TXS, ISSUER = TXS + 2;
+constexpr int NB = 4;                    // bundle buffers
+__host__ __device__ constexpr int pad16(int b) { return (b + 15) / 16 * 16; }
+}  // namespace t2d
+
+// Shared-memory layout: per direction a box of pairs (slots 0, 1 of the
+// direction) and a box of singles (slot 2).  FP32: pairs as 8-byte elements,
+// boxes of 136 cells from x0 - 4; 16-bit: pairs as 4-byte elements, boxes of
+// 144 cells from x0 - 8 (a 2-byte single's x coordinate must be a multiple of
+// 8).  A slot holds the +x and -x groups of the strip cells and the group of
+// each halo cell.
+template <class S> struct T2D {
+    static constexpr int X0 = sizeof(S) == 4 ? 4 : 8;
+    static constexpr int W = t2d::TXS + 2 * X0;
+    static constexpr int PE = 2 * (int)sizeof(S), SE = (int)sizeof(S);  // pair / single bytes
+    static constexpr int PAIR_BYTES = W * PE, SINGLE_BYTES = W * SE;
+    static constexpr int SINGLE_OFF = t2::pad128(PAIR_BYTES);
+    static constexpr int DIR_BYTES = t2::pad128(SINGLE_OFF + SINGLE_BYTES);
+    static constexpr int EPS_OFF = 7 * DIR_BYTES;
+    static constexpr int EPS_BYTES = W * 4;
+    static constexpr int BUNDLE = t2::pad128(EPS_OFF + EPS_BYTES);
+    static constexpr unsigned TX_BYTES = 7 * (PAIR_BYTES + SINGLE_BYTES) + EPS_BYTES;
+    static constexpr int NSLOT = 2 * t2d::TXS + 2;  // [dir 1 | dir 2] x strip, then the two halo cells
+    static constexpr int S_S = t2d::pad16(NSLOT * PE);
+    static constexpr int SLOT = t2d::pad16(S_S + NSLOT * SE);
+    static constexpr int SMEM = t2d::NB * BUNDLE + 3 * SLOT;
+    static constexpr int MIN_BLOCKS = sizeof(S) == 4 ? 3 : 4;
+};
+
+// The three values of one direction of a 2D cell in storage form.
+template <class S> struct DirVal2 { unsigned p; unsigned short s; };  // 16-bit
+template <> struct DirVal2<float> { float2 p; float s; };
+
+template <int MODE, class S>
+__device__ __forceinline__ DirVal2<S> to_dir2(const float *f, int d)
+{
+    DirVal2<S> v;
+    const float a = f[slot_plane(MODE, d, 0)], b = f[slot_plane(MODE, d, 1)], c = f[slot_plane(MODE, d, 2)];
+    if constexpr (sizeof(S) == 4) {
+        v.p = make_float2(a, b);
+        v.s = c;
+    } else {
+        v.p = Io<S>::pack(a, b);
+        S h;
+        if constexpr (std::is_same<S, __half>::value) h = __float2half_rn(c);
+        else h = __float2bfloat16_rn(c);
+        memcpy(&v.s, &h, 2);
+    }
+    return v;
+}
+
+template <int MODE, class S>
+__device__ __forceinline__ void from_dir2(const DirVal2<S> &v, float *f, int d)
+{
+    if constexpr (sizeof(S) == 4) {
+        f[slot_plane(MODE, d, 0)] = v.p.x;
+        f[slot_plane(MODE, d, 1)] = v.p.y;
+        f[slot_plane(MODE, d, 2)] = v.s;
+    } else {
+        const float2 ab = Io<S>::unpack(v.p);
+        S h;
+        memcpy(&h, &v.s, 2);
+        f[slot_plane(MODE, d, 0)] = ab.x;
+        f[slot_plane(MODE, d, 1)] = ab.y;
+        if constexpr (std::is_same<S, __half>::value) f[slot_plane(MODE, d, 2)] = __half2float(h);
+        else f[slot_plane(MODE, d, 2)] = __bfloat162float(h);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ DirVal2<S> bundle2_get(const unsigned char *buf, int d, int col)
+{
+    using L = T2D<S>;
+    const unsigned char *b = buf + d * L::DIR_BYTES;
+    DirVal2<S> v;
+    if constexpr (sizeof(S) == 4) {
+        v.p = reinterpret_cast<const float2 *>(b)[col];
+        v.s = reinterpret_cast<const float *>(b + L::SINGLE_OFF)[col];
+    } else {
+        v.p = reinterpret_cast<const unsigned *>(b)[col];
+        v.s = reinterpret_cast<const unsigned short *>(b + L::SINGLE_OFF)[col];
+    }
+    return v;
+}
+
+// Slot entry i: direction 1 of strip cell i (i < 128), direction 2 of strip
+// cell i - 128 (i < 256), or the group of halo cell i - 256.
+template <class S>
+__device__ __forceinline__ void slot2_put(unsigned char *slot, int i, const DirVal2<S> &v)
+{
+    using L = T2D<S>;
+    if constexpr (sizeof(S) == 4) {
+        reinterpret_cast<float2 *>(slot)[i] = v.p;
+        reinterpret_cast<float *>(slot + L::S_S)[i] = v.s;
+    } else {
+        reinterpret_cast<unsigned *>(slot)[i] = v.p;
+        reinterpret_cast<unsigned short *>(slot + L::S_S)[i] = v.s;
+    }
+}
+
+template <class S>
+__device__ __forceinline__ DirVal2<S> slot2_get(const unsigned char *slot, int i)
+{
+    using L = T2D<S>;
+    DirVal2<S> v;
+    if constexpr (sizeof(S) == 4) {
+        v.p = reinterpret_cast<const float2 *>(slot)[i];
+        v.s = reinterpret_cast<const float *>(slot + L::S_S)[i];
+    } else {
+        v.p = reinterpret_cast<const unsigned *>(slot)[i];
+        v.s = reinterpret_cast<const unsigned short *>(slot + L::S_S)[i];
+    }
+    return v;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// Copy the level-n bundle of row r into the buffer at dst (the copies
+// complete the mbarrier bar).  Every x coordinate is x0 - X0 with x0 a
+// multiple of 128, so each box starts on a 16-byte boundary.
+template <class S>
+__device__ __forceinline__ void t2d_issue(const Step2Args &P, uint32_t dst, uint32_t bar, int x0, int r, int ny)
+{
+    using L = T2D<S>;
+    const int rm = r > 0 ? r - 1 : 0, rp = r < ny - 1 ? r + 1 : ny - 1;
+    mbar_expect_tx(bar, L::TX_BYTES);
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+        const int row = d == 3 ? rm : (d == 4 ? rp : r);
+        tma_load_3d(dst + d * L::DIR_BYTES, &P.map_a, x0 - L::X0, row, d, bar);
+        tma_load_3d(dst + d * L::DIR_BYTES + L::SINGLE_OFF, &P.map_b, x0 - L::X0, row, d, bar);
+    }
+    tma_load_2d(dst + L::EPS_OFF, &P.map_eps, x0 - L::X0, r, bar);
+}
+
+// Level n+2 of strip cell t at (x, y) from level n+1.
+template <int MODE, class S>
+__device__ __forceinline__ void t2d_level2(const StepArgs &s2, const unsigned char *slot, int t, int x, int y,
+                                           const DirVal2<S> &d0, const DirVal2<S> &d3, const DirVal2<S> &d4,
+                                           const DirVal2<S> &d5, const DirVal2<S> &d6, float ie)
+{
+    constexpr int TXS = t2d::TXS;
+    const int nx = s2.nx;
+    float f[Planes<MODE>::Q];
+    from_dir2<MODE, S>(d0, f, 0);
+    // +x from x - 1: the left halo cell at the strip edge, the cell itself at the grid edge
+    from_dir2<MODE, S>(slot2_get<S>(slot, x == 0 ? t : (t == 0 ? 2 * TXS : t - 1)), f, 1);
+    // -x from x + 1: the right halo cell at the strip edge, the cell itself at the grid edge
+    from_dir2<MODE, S>(slot2_get<S>(slot, x == nx - 1 ? TXS + t : (t == TXS - 1 ? 2 * TXS + 1 : TXS + t + 1)), f, 2);
+    from_dir2<MODE, S>(d3, f, 3);
+    from_dir2<MODE, S>(d4, f, 4);
+    from_dir2<MODE, S>(d5, f, 5);
+    from_dir2<MODE, S>(d6, f, 6);
+    FloatCell cell{f};
+    update_cell<MODE, false, false, false, true>(cell, x, y, 0, ie, s2, 1.0f, true);
+    store_cell<MODE, S>(s2, y * s2.nxp + x, f);
+}
+
+template <int MODE, class S>
+__device__ __forceinline__ void step2d_body(const Step2Args &P)
+{
+    using L = T2D<S>;
+    constexpr int TXS = t2d::TXS;
+    extern __shared__ __align__(1024) unsigned char t2sm[];
+    __shared__ __align__(8) unsigned long long bars[t2d::NB];
+    const StepArgs &s1 = P.s1, &s2 = P.s2;
+    const int nx = s1.nx, ny = s1.ny;
+    const int x0 = blockIdx.x * TXS;
+    const int t = threadIdx.x;
+    // row chunk [y0, y1); level n+1 runs over [pa, pb]
+    const int y0 = blockIdx.y * P.zc, y1 = min(ny, y0 + P.zc);
+    const int pa = max(y0 - 1, 0), pb = min(y1, ny - 1);
+    const int nl1 = pb - pa + 1;  // >= 2 (ny >= 2)
+    const uint32_t bar0 = smem_u32(&bars[0]), buf0 = smem_u32(t2sm);
+    unsigned char *slots = t2sm + t2d::NB * L::BUNDLE;
+
+    if (t == t2d::ISSUER) {
+        for (int b = 0; b < t2d::NB; ++b) mbar_init(bar0 + 8 * b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == t2d::ISSUER)
+        for (int j = 0; j < t2d::NB && j < nl1; ++j)
+            t2d_issue<S>(P, buf0 + j * L::BUNDLE, bar0 + 8 * j, x0, pa + j, ny);
+
+    // this thread's cell: a strip cell, the left or right halo cell, or none
+    const bool strip = t < TXS;
+    const int x = strip ? x0 + t : (t == t2d::HALO ? x0 - 1 : (t == t2d::HALO + 1 ? x0 + TXS : -1));
+    const bool live = x >= 0 && x < nx;
+    const int col = x - x0 + L::X0;
+
+    DirVal2<S> d0_prev{}, d3_prev{}, d3_pp{}, d5_prev{}, d6_prev{}, d4_cur{};
+    float ie_prev = 1.f;
+    bool failed = false;
+    int consumed = 0;
+    for (int j = 0; j < nl1; ++j) {
+        const int p = pa + j;
+        const unsigned char *buf = t2sm + (j % t2d::NB) * L::BUNDLE;
+        unsigned char *slot = slots + (p % 3) * L::SLOT;
+        bool bad = false;
+        if (!failed) {
+            bad = !mbar_wait_bounded(bar0 + 8 * (j % t2d::NB), (j / t2d::NB) & 1);
+            if (!bad) consumed = j + 1;
+        }
+        DirVal2<S> d0_cur{}, d3_cur{}, d5_cur{}, d6_cur{};
+        float ie_cur = 1.f;
+        if (live && !failed && !bad) {
+            float f[Planes<MODE>::Q];
+            from_dir2<MODE, S>(bundle2_get<S>(buf, 0, col), f, 0);
+            from_dir2<MODE, S>(bundle2_get<S>(buf, 1, x > 0 ? col - 1 : col), f, 1);
+            from_dir2<MODE, S>(bundle2_get<S>(buf, 2, x < nx - 1 ? col + 1 : col), f, 2);
+            from_dir2<MODE, S>(bundle2_get<S>(buf, 3, col), f, 3);
+            from_dir2<MODE, S>(bundle2_get<S>(buf, 4, col), f, 4);
+            from_dir2<MODE, S>(bundle2_get<S>(buf, 5, col), f, 5);
+            from_dir2<MODE, S>(bundle2_get<S>(buf, 6, col), f, 6);
+            const float ie = reinterpret_cast<const float *>(buf + L::EPS_OFF)[col];
+            FloatCell cell{f};
+            update_cell<MODE, false, false, false, true>(cell, x, p, 0, ie, s1, 1.0f, strip && p >= y0 && p < y1);
+            if (strip) {
+                slot2_put<S>(slot, t, to_dir2<MODE, S>(f, 1));
+                slot2_put<S>(slot, TXS + t, to_dir2<MODE, S>(f, 2));
+                d0_cur = to_dir2<MODE, S>(f, 0);
+                d3_cur = to_dir2<MODE, S>(f, 3);
+                d4_cur = to_dir2<MODE, S>(f, 4);
+                d5_cur = to_dir2<MODE, S>(f, 5);
+                d6_cur = to_dir2<MODE, S>(f, 6);
+                ie_cur = ie;
+            } else {
+                // the left halo cell gives the strip its +x group, the right one its -x group
+                slot2_put<S>(slot, 2 * TXS + (t - t2d::HALO),
+                             t == t2d::HALO ? to_dir2<MODE, S>(f, 1) : to_dir2<MODE, S>(f, 2));
+            }
+        }
+        // level n+1 of row p is complete and its bundle buffer free
+        failed = __syncthreads_or(failed || bad) != 0;
+        if (!failed && t == t2d::ISSUER && j + t2d::NB < nl1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            t2d_issue<S>(P, buf0 + (j % t2d::NB) * L::BUNDLE, bar0 + 8 * (j % t2d::NB), x0, p + t2d::NB, ny);
+        }
+        // level n+2 of row p - 1; at p - 1 == 0 the +y pull clamps to the row itself
+        if (!failed && strip && live && p - 1 >= y0)
+            t2d_level2<MODE, S>(s2, slots + ((p - 1) % 3) * L::SLOT, t, x, p - 1, d0_prev,
+                                p - 1 == 0 ? d3_prev : d3_pp, d4_cur, d5_prev, d6_prev, ie_prev);
+        d3_pp = d3_prev;
+        d3_prev = d3_cur;
+        d0_prev = d0_cur;
+        d5_prev = d5_cur;
+        d6_prev = d6_cur;
+        ie_prev = ie_cur;
+    }
+    if (failed) {
+        if (t == t2d::ISSUER) {
+            atomicOr(s1.status, 1);
+            const int issued = min(consumed + t2d::NB, nl1);
+            for (int k = consumed; k < issued; ++k)
+                mbar_wait_bounded(bar0 + 8 * (k % t2d::NB), (k / t2d::NB) & 1);
+        }
+        return;
+    }
+    // the last row of the grid pulls its -y group from itself (Eq. 4)
+    if (y1 == ny && strip && live)
+        t2d_level2<MODE, S>(s2, slots + ((ny - 1) % 3) * L::SLOT, t, x, ny - 1, d0_prev, d3_pp, d4_cur, d5_prev,
+                            d6_prev, ie_prev);
+}
+
+template <int MODE, class S>
+__global__ void __launch_bounds__(t2d::THREADS, T2D<S>::MIN_BLOCKS) step2d_kernel(const __grid_constant__ Step2Args P)
+{
+    step2d_body<MODE, S>(P);
+}
+
 // Sums cnt staged steps of face fields into the FP64 DFT accumulators in step
 // order, with the same fma as the direct path: one thread per (face cell,
 // component), reads coalesced along the cells.  Slot s holds the faces in
@@ -1597,6 +1901,89 @@ cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t 
     return cudaGetLastError();
 }
 
+// ---- host side of the 2D two-step pass
+int g_step2d_bps[kMaxDevices][6];
+
+template <int MODE, class S>
+cudaError_t step2d_setup(int &blocks_per_sm)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_step2_mu);
+    int &bps = g_step2d_bps[dev][MODE * 3 + storage_slot<S>()];
+    if (bps == 0) {
+        e = cudaFuncSetAttribute(step2d_kernel<MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, T2D<S>::SMEM);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2d_kernel<MODE, S>, t2d::THREADS, T2D<S>::SMEM);
+        if (e != cudaSuccess) return e;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        bps = n;
+    }
+    blocks_per_sm = bps;
+    return cudaSuccess;
+}
+
+// Whether 2D two-step passes pay: the strips times chunks of at least 16 rows
+// fill two waves of resident blocks (smaller grids sit in L2, where single
+// steps cost no HBM traffic anyway); boxes must fit the row.
+template <int MODE, class S>
+bool step2d_worthwhile_t(int nx, int ny)
+{
+    if (nx < 256 || ny < 16) return false;
+    int bps = 0;
+    if (step2d_setup<MODE, S>(bps) != cudaSuccess) return false;
+    const long long strips = (nx + t2d::TXS - 1) / t2d::TXS;
+    return strips * std::max(1, ny / 16) >= 2LL * std::max(1, sm_count()) * bps;
+}
+
+template <int MODE, class S>
+cudaError_t launch_step2d_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+{
+    using L = T2D<S>;
+    if (s1.nz != 1 || s1.nx < 256 || s1.ny < 16 || s1.nxp % 32 || s1.P % 32) return cudaErrorInvalidValue;
+    int bps = 0;
+    cudaError_t e = step2d_setup<MODE, S>(bps);
+    if (e != cudaSuccess) return e;
+    Step2Args P;
+    std::memset(&P, 0, sizeof P);
+    P.s1 = s1;
+    P.s2 = s2;
+    const char *f = static_cast<const char *>(s1.fin_q[0]);
+    const cuuint64_t nxp = s1.nxp, ny = s1.ny, Pn = (cuuint64_t)s1.P;
+    // direction i: its pairs at 3 i P elements, its singles at (3 i + 2) P
+    const cuuint64_t dims[3] = {nxp, ny, 7};
+    const cuuint64_t sp[2] = {L::PE * nxp, 3 * L::SE * Pn}, ss[2] = {L::SE * nxp, 3 * L::SE * Pn};
+    const cuuint32_t box[3] = {L::W, 1, 1};
+    bool ok = encode_map(&P.map_a, sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                         3, f, dims, sp, box) &&
+              encode_map(&P.map_b, sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                         3, f + 2 * L::SE * Pn, dims, ss, box);
+    {
+        const cuuint64_t de[2] = {nxp, ny}, se[1] = {4 * nxp};
+        const cuuint32_t be[2] = {L::W, 1};
+        ok = ok && encode_map(&P.map_eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s1.inv_eps, de, se, be);
+    }
+    if (!ok) return cudaErrorInvalidValue;
+    if (s1.line_on) {
+        line2_kernel<MODE><<<1, 512, 0, s>>>(P.s1, P.s2);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // row chunks as the 3D pass's z chunks: about 40 rows, more and shorter
+    // (at least 8 rows) where that would not fill two waves
+    const long long strips = (s1.nx + t2d::TXS - 1) / t2d::TXS;
+    const long long cap = (long long)std::max(1, sm_count()) * bps;
+    int nyc = std::max(1, (s1.ny + 20) / 40);
+    while (strips * nyc < 2 * cap && (s1.ny + nyc) / (nyc + 1) >= 8) ++nyc;
+    P.zc = (s1.ny + nyc - 1) / nyc;
+    const dim3 grid((unsigned)strips, (s1.ny + P.zc - 1) / P.zc, 1);
+    step2d_kernel<MODE, S><<<grid, t2d::THREADS, L::SMEM, s>>>(P);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int sm_count()
@@ -1665,22 +2052,34 @@ cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_step2(int storage, const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+cudaError_t launch_step2(int mode, int storage, const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
 {
-    switch (storage) {
-    case 0: return launch_step2_t<float>(s1, s2, s);
-    case 1: return launch_step2_t<__half>(s1, s2, s);
-    case 2: return launch_step2_t<__nv_bfloat16>(s1, s2, s);
+    switch (mode * 3 + storage) {
+    case 0: return launch_step2d_t<0, float>(s1, s2, s);
+    case 1: return launch_step2d_t<0, __half>(s1, s2, s);
+    case 2: return launch_step2d_t<0, __nv_bfloat16>(s1, s2, s);
+    case 3: return launch_step2d_t<1, float>(s1, s2, s);
+    case 4: return launch_step2d_t<1, __half>(s1, s2, s);
+    case 5: return launch_step2d_t<1, __nv_bfloat16>(s1, s2, s);
+    case 6: return launch_step2_t<float>(s1, s2, s);
+    case 7: return launch_step2_t<__half>(s1, s2, s);
+    case 8: return launch_step2_t<__nv_bfloat16>(s1, s2, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-bool step2_worthwhile(int storage, int nx, int ny, int nz)
+bool step2_worthwhile(int mode, int storage, int nx, int ny, int nz)
 {
-    switch (storage) {
-    case 0: return step2_worthwhile_t<float>(nx, ny, nz);
-    case 1: return step2_worthwhile_t<__half>(nx, ny, nz);
-    case 2: return step2_worthwhile_t<__nv_bfloat16>(nx, ny, nz);
+    switch (mode * 3 + storage) {
+    case 0: return step2d_worthwhile_t<0, float>(nx, ny);
+    case 1: return step2d_worthwhile_t<0, __half>(nx, ny);
+    case 2: return step2d_worthwhile_t<0, __nv_bfloat16>(nx, ny);
+    case 3: return step2d_worthwhile_t<1, float>(nx, ny);
+    case 4: return step2d_worthwhile_t<1, __half>(nx, ny);
+    case 5: return step2d_worthwhile_t<1, __nv_bfloat16>(nx, ny);
+    case 6: return step2_worthwhile_t<float>(nx, ny, nz);
+    case 7: return step2_worthwhile_t<__half>(nx, ny, nz);
+    case 8: return step2_worthwhile_t<__nv_bfloat16>(nx, ny, nz);
     default: return false;
     }
 }

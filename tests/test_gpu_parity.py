@@ -380,6 +380,53 @@ def test_dft_same_for_any_step_split(mode):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("mode,shape,wave", [("ez", (2176, 1800, 1), False), ("hz", (2100, 1750, 1), False),
+                                             ("ez", (2080, 1800, 1), True), ("hz", (2200, 1760, 1), True)])
+def test_two_step_fusion_2d_matches_single_steps(mode, shape, wave, storage):
+    """Two updates per pass in 2D (strips of 128 cells marching along y, level
+    n staged in shared memory by TMA, x halos, clamped pulls at the grid
+    edges, row chunks): the same populations, DFT accumulators and far field
+    as single steps, bit for bit, in every storage type, from a random state
+    or driven by the plane wave across its DFT window, over an odd step count.
+    The grids are large enough for the pass to be taken, which the library
+    reports."""
+    nx, ny, _ = shape
+    if wave:
+        # a dielectric block just inside the total-field region, so that its
+        # scattered wave reaches the NTFF faces within the run
+        eps = np.ones((1, ny, nx), np.float32)
+        eps[0, ny // 2 - 100:ny // 2 + 100, 14:40] = 3.0
+        wv = W.axis_wave(mode, shape, 8, 12.0, gap_ntff=2, gap_tf=2)
+        p = W.Problem("fuse2d_wave", mode, shape, eps, 8, 0.3, wv, 72, 1)
+        init, steps = None, 61
+    else:
+        eps = W.random_eps(shape, 1.0, 6.0, 5)
+        p = W.Problem("fuse2d", mode, shape, eps, 5, 0.3, None, 9, 1)
+        init, steps = W.random_state_f32(mode, shape, 6), 9
+    a = gpu_solver(p, storage=storage, init=init, steps=0)
+    a.set_step_fusion(1)
+    b = gpu_solver(p, storage=storage, init=init, steps=0)
+    b.set_step_fusion(2)
+    assert a.step_fusion() == 1 and b.step_fusion() == 2
+    if wave:
+        a.set_dft_window(30, 1)
+        b.set_dft_window(30, 1)
+    a.step(steps)
+    b.step(steps - 4)
+    b.step(4)
+    assert a.time == b.time == steps
+    assert np.array_equal(a.populations(), b.populations())
+    if wave:
+        assert np.array_equal(a.dft(), b.dft())
+        assert np.abs(a.dft()).max() > 0
+        assert a.incident_amplitude() == b.incident_amplitude()
+        th, ph = angles(mode)
+        assert np.array_equal(a.far_field(th, ph), b.far_field(th, ph))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("shape,seed,wave", [((300, 130, 40), 3, False), ((350, 121, 33), 4, False),
                                              ((256, 168, 40), 5, True)])
 def test_two_step_fusion_matches_single_steps(shape, seed, wave, storage):
