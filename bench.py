@@ -60,11 +60,13 @@ def b_cell(mode: str, storage: str) -> int:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the step kernel's source: step.cu and the StepArgs definition."""
+    """Hash of the step kernels' source: step.cu, step2.cu, step_cell.cuh and
+    the StepArgs definition."""
     csrc = os.path.join(ROOT, "paper_2510_11042_gb300", "csrc")
     h = hashlib.sha256()
-    with open(os.path.join(csrc, "step.cu"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("step.cu", "step2.cu", "step_cell.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     hdr = open(os.path.join(csrc, "lbem_internal.cuh")).read()
     i = hdr.index("struct StepArgs {")
     h.update(hdr[i:hdr.index("};", i)].encode())
@@ -511,12 +513,12 @@ def run_probe_2d(dev, n=4096, updates=60):
 
 
 # ------------------------------------------------------------------ other step-kernel instantiations
-def run_variants_3d(dev, updates=45):
-    """The step kernel's other instantiations on the 384^3 sphere, FP32: single
-    steps (lbem_set_step_fusion(1), the kernel that runs when two-step passes
-    do not apply), with a mu_r map (mu_r = 2 in the sphere; 4 more bytes per
-    cell for 1/mu_r) and with the closed-form source at 30 degrees (both take
-    single steps)."""
+def run_variants_3d(dev, updates=44, storages=("f32", "f16")):
+    """The step kernel's other instantiations on the 384^3 sphere: single steps
+    (lbem_set_step_fusion(1)), and with a mu_r map (mu_r = 2 in the sphere; 4
+    more bytes per cell for 1/mu_r) and with the closed-form source at 30
+    degrees, each with the pass lbem_step takes by default (two updates per
+    pass where the library reports it) and with single steps."""
     import dataclasses
     import torch
     from paper_2510_11042_gb300 import lbem
@@ -527,17 +529,16 @@ def run_variants_3d(dev, updates=45):
     oblique = dataclasses.replace(p.wave, direction=(math.sin(th), 0.0, math.cos(th)),
                                   polarization=(math.cos(th), 0.0, -math.sin(th)), analytic=True,
                                   origin=tuple(float(v) for v in p.wave.tf_lo))
-    out = {"workload": "sphere 384^3 (the bench workload), FP32 storage"}
-    for name, mu, wave, bc in (("single_step", False, p.wave, b_cell("3d", "f32")),
-                               ("magnetic_mu2", True, p.wave, b_cell("3d", "f32") + 4),
-                               ("closed_form_source_30deg", False, oblique, b_cell("3d", "f32") + 4)):
-        s = lbem.Solver(p.shape, p.eps, "3d", "f32", p.absorber_width, p.sigma_max, device=dev)
-        s.set_step_fusion(1)
+    out = {"workload": "sphere 384^3 (the bench workload)"}
+
+    def timed(st, fuse, mu, wave, dft):
+        s = lbem.Solver(p.shape, p.eps, "3d", st, p.absorber_width, p.sigma_max, device=dev)
+        s.set_step_fusion(fuse)
         if mu:
             s.set_permeability(np.where(p.eps > 1.0, np.float32(2.0), np.float32(1.0)))
         s.inject(wave)
-        s.step(5)
-        if name == "single_step":   # like a bench step: the DFT window on
+        s.step(6)
+        if dft:   # like a bench step: the DFT window on
             s.set_dft_window(s.time + 1, 1)
         torch.cuda.synchronize(dev)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -546,12 +547,29 @@ def run_variants_3d(dev, updates=45):
         ev[1].record(s.stream)
         torch.cuda.synchronize(dev)
         ms = ev[0].elapsed_time(ev[1]) / updates
-        gbs = bc * cells / (ms / 1e3) / 1e9
-        out[name] = {"kernel_ms": round(ms, 4), "mlups": round(cells / (ms / 1e3) / 1e6, 1),
-                     "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+        spp = s.step_fusion()
         s.close()
         del s
         torch.cuda.empty_cache()
+        return ms, spp
+
+    for st in storages:
+        base = b_cell("3d", st)
+        for name, mu, wave, bc, fuses in (("single_step", False, p.wave, base, (1,)),
+                                           ("magnetic_mu2", True, p.wave, base + 4, (2, 1)),
+                                           ("closed_form_source_30deg", False, oblique, base + 4, (2, 1))):
+            rec = {}
+            for fuse in fuses:
+                ms, spp = timed(st, fuse, mu, wave, name == "single_step")
+                gbs = bc * cells / (ms / 1e3) / 1e9
+                rec[fuse] = {"kernel_ms": round(ms, 4), "mlups": round(cells / (ms / 1e3) / 1e6, 1),
+                             "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                             "steps_per_pass": spp}
+            entry = dict(rec[fuses[0]])
+            if len(fuses) == 2:
+                entry["single_step"] = rec[1]
+                entry["speedup_vs_single_step"] = round(rec[1]["kernel_ms"] / rec[2]["kernel_ms"], 3)
+            out[name if st == "f32" else f"{name}_{st}"] = entry
     return out
 
 
@@ -754,8 +772,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-updates", type=float, default=2)
-    ap.add_argument("--section", default="all", choices=["all", "adjoint_probe", "probe_2d"],
-                    help="adjoint_probe / probe_2d: only that measurement (profiling)")
+    ap.add_argument("--section", default="all", choices=["all", "adjoint_probe", "probe_2d", "variants_3d"],
+                    help="adjoint_probe / probe_2d / variants_3d: only that measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -765,12 +783,13 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.section in ("adjoint_probe", "probe_2d"):
+    if args.section in ("adjoint_probe", "probe_2d", "variants_3d"):
         import torch
         from paper_2510_11042_gb300 import build as lib_build
         lib_build.build()
         dev = torch.device("cuda", local_rank)
-        fn = _adjoint_probe_3d if args.section == "adjoint_probe" else run_probe_2d
+        fn = {"adjoint_probe": _adjoint_probe_3d, "probe_2d": run_probe_2d,
+              "variants_3d": run_variants_3d}[args.section]
         print(json.dumps(fn(dev)), flush=True)
         return
     if world > 1:

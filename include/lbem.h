@@ -204,15 +204,17 @@ int32_t lbem_far_field(lbem_handle h, const double *theta_host, const double *ph
                        int32_t n, double *s2_host, double *amp_host);
 
 /* Temporal blocking (Eq. 1 applied twice per pass over memory):
- * steps_per_pass = 2 (the default) lets lbem_step advance 3D grids of any
- * storage without a mu_r map or closed-form source two steps per pass over
- * the populations: a fused kernel keeps the intermediate state of each xy tile
- * (32 x 8 cells plus edge halos) in shared memory while it marches through a
- * chunk of z planes, bitwise the same result as two single steps (16-bit
- * storage rounds the intermediate state as a single step stores it).  It is
- * taken where its blocks fill at least one wave of resident blocks; other
- * grids, and a last odd step, take single steps.  1 always takes single
- * steps.  Anything else: LBEM_ERR_ARG. */
+ * steps_per_pass = 2 (the default) lets lbem_step advance grids of any mode
+ * and storage, with or without a mu_r map, two steps per pass over the
+ * populations: a fused kernel keeps the intermediate state of each tile (3D:
+ * 32 x 8 cells in FP32, 32 x 16 in FP16/BF16, marching through a chunk of z
+ * planes; 2D: 128-cell strips marching along y) plus its edge halos in shared
+ * memory, bitwise the same result as two single steps (16-bit storage rounds
+ * the intermediate state as a single step stores it).  It is taken where its
+ * blocks fill the GPU (one wave of resident blocks in 3D, two in 2D, where
+ * smaller grids sit in L2); other grids, the closed-form source (bound by its
+ * wave evaluations, not by memory) and a last odd step take single steps.
+ * 1 always takes single steps.  Anything else: LBEM_ERR_ARG. */
 int32_t lbem_set_step_fusion(lbem_handle h, int32_t steps_per_pass);
 
 /* The steps per pass lbem_step takes on this handle as it is now configured:

@@ -783,12 +783,15 @@ static void stage_slot(lbem_ctx *h, StepArgs &a, unsigned mask)
     ++h->xs_cnt;
 }
 
-// Whether lbem_step takes two steps per pass: fusion on, no mu_r map or
-// closed-form source, on a grid whose blocks fill the GPU.
+// The kernel variant of the update: 0 plain, 1 with the mu_r map, 2 with the
+// closed-form source.
+static int step_variant(const lbem_ctx *h) { return h->analytic ? 2 : (h->mu_on ? 1 : 0); }
+
+// Whether lbem_step takes two steps per pass: fusion on, on a grid whose
+// blocks fill the GPU.
 static bool two_step_passes(lbem_ctx *h)
 {
-    return h->fuse == 2 && !h->analytic && !h->mu_on &&
-           step2_worthwhile(h->g.mode, h->g.storage, h->g.nx, h->g.ny, h->g.nz);
+    return h->fuse == 2 && step2_worthwhile(h->g.mode, h->g.storage, step_variant(h), h->g.nx, h->g.ny, h->g.nz);
 }
 
 int32_t lbem_step(lbem_handle h, int64_t n)
@@ -812,7 +815,7 @@ int32_t lbem_step(lbem_handle h, int64_t n)
             const int cnt0 = h->xs_cnt;
             stage_slot(h, a, h->xs_allmask);
             stage_slot(h, a2, h->xs_allmask);
-            cudaError_t e = launch_step2(h->g.mode, h->g.storage, a, a2, h->stream);
+            cudaError_t e = launch_step2(h->g.mode, h->g.storage, step_variant(h), a, a2, h->stream);
             if (e != cudaSuccess) {
                 h->xs_cnt = cnt0;   // the claimed slots hold nothing
                 return cuda_fail(h, e, "two-step kernel launch");

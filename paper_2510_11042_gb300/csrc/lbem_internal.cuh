@@ -271,13 +271,15 @@ cudaError_t launch_batch(int mode, int storage, const BatchArgs &b, int grid, cu
 cudaError_t launch_barrier_selftest(const BatchArgs &b, cudaStream_t s);
 int batch_max_blocks_per_sm(int mode, int storage);
 cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s);
-// Two steps in one pass (any mode and storage, no mu_r map or closed-form
-// source): s1 the first step's arguments (reads fin_q), s2 the second's
-// (writes fout_q, which must not alias s1.fin_q); with the incident line on,
-// a one-block launch before it updates the line for both steps (two launches
-// in all).
-cudaError_t launch_step2(int mode, int storage, const StepArgs &s1, const StepArgs &s2, cudaStream_t s);
-bool step2_worthwhile(int mode, int storage, int nx, int ny, int nz);
+// Two steps in one pass (any mode and storage; variant 0: plain update, 1:
+// with the per-cell mu_r map; 2, the closed-form source, is refused and
+// reported not worthwhile): s1 the first
+// step's arguments (reads fin_q), s2 the second's (writes fout_q, which must
+// not alias s1.fin_q); with the incident line on, a one-block launch before
+// it updates the line for both steps (two launches in all).
+cudaError_t launch_step2(int mode, int storage, int variant, const StepArgs &s1, const StepArgs &s2,
+                         cudaStream_t s);
+bool step2_worthwhile(int mode, int storage, int variant, int nx, int ny, int nz);
 // The step kernel with a per-cell mu_r (a.inv_mu), Eq. 2's h_0 = (mu_r - 1) H
 cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_t s);
 // The step kernel with the analytic plane-wave source (a.tfsf == 2; reads a.inv_mu)

@@ -379,6 +379,41 @@ def test_dft_same_for_any_step_split(mode):
     assert rel_l2(got, exp) <= TOL
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("mode,shape", [("3d", (300, 130, 40)), ("ez", (2176, 1800, 1)), ("hz", (2100, 1750, 1))])
+def test_two_step_with_mu_map_matches_single_steps(mode, shape, storage):
+    """The two-step pass with a per-cell mu_r map (random mu_r in [1, 3],
+    random eps_r, the incident line): the same populations, DFT accumulators
+    and far field as single steps, bit for bit, over an odd step count that
+    crosses the DFT window.  The closed-form source keeps single steps on the
+    same grid (its update is bound by the wave evaluations, not by memory)."""
+    from test_gpu_oblique import oblique_problem
+    wv = W.axis_wave(mode, shape, 6, 10.0, gap_ntff=2, gap_tf=3)
+    eps = W.random_eps(shape, 1.0, 4.0, 21)
+    mu = W.random_eps(shape, 1.0, 3.0, 22)
+    p = dataclasses.replace(W.Problem("fuse_mu", mode, shape, eps, 6, 0.3, wv, 31, 1), mu=mu)
+    c = gpu_solver(W.with_steps(oblique_problem(mode, shape, lam=10.0), 31), storage=storage, steps=0)
+    assert c.step_fusion() == 1
+    c.close()
+    a = gpu_solver(p, storage=storage, steps=0)
+    a.set_step_fusion(1)
+    b = gpu_solver(p, storage=storage, steps=0)
+    b.set_step_fusion(2)
+    assert a.step_fusion() == 1 and b.step_fusion() == 2
+    a.set_dft_window(8, 1)
+    b.set_dft_window(8, 1)
+    a.step(p.steps)
+    b.step(p.steps - 4)
+    b.step(4)
+    assert a.time == b.time == p.steps
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.dft(), b.dft())
+    th, ph = angles(mode)
+    assert np.array_equal(a.far_field(th, ph), b.far_field(th, ph))
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("mode,shape,wave", [("ez", (2176, 1800, 1), False), ("hz", (2100, 1750, 1), False),
                                              ("ez", (2080, 1800, 1), True), ("hz", (2200, 1760, 1), True)])
