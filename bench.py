@@ -509,11 +509,18 @@ def run_probe_2d(dev, n=4096, updates=60):
             torch.cuda.empty_cache()
         out[st] = dict(rec[2], single_step=rec[1], speedup_vs_single_step=round(rec[1]["kernel_ms"] /
                                                                                 rec[2]["kernel_ms"], 3))
+        # the two-step kernel's own DRAM traffic (ncu, committed summary), over the time of its launch
+        traffic = traffic_from_profile(f"cylinder_{n}_ez", st) if rec[2]["steps_per_pass"] == 2 else None
+        if traffic:
+            gbs_t = traffic / (2 * rec[2]["kernel_ms"] / 1e3) / 1e9
+            out[st]["dram_traffic_per_launch"] = traffic
+            out[st]["dram_traffic_gbs"] = round(gbs_t, 1)
+            out[st]["dram_traffic_frac"] = round(gbs_t / hbm, 4)
     return out
 
 
 # ------------------------------------------------------------------ other step-kernel instantiations
-def run_variants_3d(dev, updates=44, storages=("f32", "f16")):
+def run_variants_3d(dev, updates=44, storages=("f32", "f16"), n=384):
     """The step kernel's other instantiations on the 384^3 sphere: single steps
     (lbem_set_step_fusion(1)), and with a mu_r map (mu_r = 2 in the sphere; 4
     more bytes per cell for 1/mu_r) and with the closed-form source at 30
@@ -522,14 +529,14 @@ def run_variants_3d(dev, updates=44, storages=("f32", "f16")):
     import dataclasses
     import torch
     from paper_2510_11042_gb300 import lbem
-    p = W.sphere_problem()
+    p = W.sphere_problem(n=n)
     cells = int(np.prod(p.shape))
     hbm, _ = peaks()
     th = math.radians(30.0)
     oblique = dataclasses.replace(p.wave, direction=(math.sin(th), 0.0, math.cos(th)),
                                   polarization=(math.cos(th), 0.0, -math.sin(th)), analytic=True,
                                   origin=tuple(float(v) for v in p.wave.tf_lo))
-    out = {"workload": "sphere 384^3 (the bench workload)"}
+    out = {"workload": f"sphere {n}^3" + (" (the bench workload)" if n == 384 else "")}
 
     def timed(st, fuse, mu, wave, dft):
         s = lbem.Solver(p.shape, p.eps, "3d", st, p.absorber_width, p.sigma_max, device=dev)
@@ -788,9 +795,11 @@ def main():
         from paper_2510_11042_gb300 import build as lib_build
         lib_build.build()
         dev = torch.device("cuda", local_rank)
-        fn = {"adjoint_probe": _adjoint_probe_3d, "probe_2d": run_probe_2d,
-              "variants_3d": run_variants_3d}[args.section]
-        print(json.dumps(fn(dev)), flush=True)
+        if args.section == "variants_3d":
+            out = run_variants_3d(dev, n=args.size)
+        else:
+            out = {"adjoint_probe": _adjoint_probe_3d, "probe_2d": run_probe_2d}[args.section](dev)
+        print(json.dumps(out), flush=True)
         return
     if world > 1:
         import torch
