@@ -47,6 +47,7 @@ struct lbem_ctx {
     size_t x32_cap = 0, tab32_cap = 0;
     bool ff_fp64 = false;       // LBEM_FAR_FIELD_FP64: 3D projection by the FP64 kernels
     int fuse = 2;               // steps per pass over the populations (lbem_set_step_fusion)
+    int share = 1;              // grids stepping beside this one (the lanes of a batched run)
     // deferred DFT of NTFF faces (see dft_flush_x_kernel)
     float *xstage = nullptr;    // [kXStage][NC][xs_n]
     size_t xstage_floats = 0;
@@ -791,7 +792,8 @@ static int step_variant(const lbem_ctx *h) { return h->analytic ? 2 : (h->mu_on 
 // blocks fill the GPU.
 static bool two_step_passes(lbem_ctx *h)
 {
-    return h->fuse == 2 && step2_worthwhile(h->g.mode, h->g.storage, step_variant(h), h->g.nx, h->g.ny, h->g.nz);
+    return h->fuse == 2 &&
+           step2_worthwhile(h->g.mode, h->g.storage, step_variant(h), h->g.nx, h->g.ny, h->g.nz, h->share);
 }
 
 int32_t lbem_step(lbem_handle h, int64_t n)
@@ -815,7 +817,7 @@ int32_t lbem_step(lbem_handle h, int64_t n)
             const int cnt0 = h->xs_cnt;
             stage_slot(h, a, h->xs_allmask);
             stage_slot(h, a2, h->xs_allmask);
-            cudaError_t e = launch_step2(h->g.mode, h->g.storage, step_variant(h), a, a2, h->stream);
+            cudaError_t e = launch_step2(h->g.mode, h->g.storage, step_variant(h), a, a2, h->stream, h->share);
             if (e != cudaSuccess) {
                 h->xs_cnt = cnt0;   // the claimed slots hold nothing
                 return cuda_fail(h, e, "two-step kernel launch");
@@ -1097,9 +1099,11 @@ static int split_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t ch
             const int64_t k = std::min<int64_t>(todo[j], kLaneSteps);
             cudaStream_t own = h->stream;
             h->stream = b->lanes[j % L];
+            h->share = L;   // L grids step beside each other on the lanes
             const int64_t l0 = h->launches;
             const int rc = lbem_step(h, k);
             h->stream = own;
+            h->share = 1;
             if (rc != LBEM_OK) return bfail(b, rc, "step of problem %d: %s", i, h->err);
             b->launches += h->launches - l0;
             left[i] -= k;

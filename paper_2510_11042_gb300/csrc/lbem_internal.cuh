@@ -13,9 +13,10 @@
 namespace lbem {
 
 constexpr int kMaxDevices = 64;  // per-device set-up caches
-// Streaming multiprocessors of the current device (queried once per device;
-// 0 if the query fails).
+// Streaming multiprocessors and L2 bytes of the current device (queried once
+// per device; 0 if the query fails).
 int sm_count();
+long long l2_bytes();
 
 constexpr int kMaxQ = 42;        // 2 families x 7 directions x 3 components (3D)
 constexpr int kMaxFaces = 6;
@@ -277,9 +278,11 @@ cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s
 // step's arguments (reads fin_q), s2 the second's (writes fout_q, which must
 // not alias s1.fin_q); with the incident line on, a one-block launch before
 // it updates the line for both steps (two launches in all).
+// share: how many grids step concurrently beside each other (the lanes of a
+// batched run), which the choice and the launch shape take into account.
 cudaError_t launch_step2(int mode, int storage, int variant, const StepArgs &s1, const StepArgs &s2,
-                         cudaStream_t s);
-bool step2_worthwhile(int mode, int storage, int variant, int nx, int ny, int nz);
+                         cudaStream_t s, int share = 1);
+bool step2_worthwhile(int mode, int storage, int variant, int nx, int ny, int nz, int share = 1);
 // The step kernel with a per-cell mu_r (a.inv_mu), Eq. 2's h_0 = (mu_r - 1) H
 cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_t s);
 // The step kernel with the analytic plane-wave source (a.tfsf == 2; reads a.inv_mu)

@@ -327,6 +327,21 @@ int max_blocks_t()
 
 }  // namespace
 
+long long l2_bytes()
+{
+    static std::mutex mu;
+    static long long cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev) != cudaSuccess) return 0;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 int sm_count()
 {
     static std::mutex mu;

@@ -1044,21 +1044,28 @@ cudaError_t launch_step2_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t 
 
 // ---- host side of the 2D two-step pass
 
-// Whether 2D two-step passes pay: the strips times chunks of at least 16 rows
-// fill two waves of resident blocks (smaller grids sit in L2, where single
-// steps cost no HBM traffic anyway); boxes must fit the row.
+// Whether 2D two-step passes pay: the population buffers of the grids
+// stepping together exceed L2 by a fifth (below that a single step's traffic
+// stays in L2; measured on EZ cylinders per update, single step against
+// two-step pass: 768^2 FP32 (99 MB) 0.0144 / 0.0173 ms, 1024^2 FP32 (176 MB)
+// 0.0307 / 0.0231, 1024^2 FP16 (88 MB) 0.0164 / 0.0205, 2048^2 FP16 (352 MB)
+// 0.0647 / 0.0531), and the strips times chunks of 16 rows fill half a wave
+// of resident blocks; boxes must fit the row.
 template <int MODE, class S, int V>
-bool step2d_worthwhile_t(int nx, int ny)
+bool step2d_worthwhile_t(int nx, int ny, int share)
 {
     if (nx < 256 || ny < 16) return false;
+    const long long nxp = (nx + 31) / 32 * 32;
+    const long long pop_bytes = 2LL * Planes<MODE>::Q * nxp * ny * (long long)sizeof(S);
+    if (5 * pop_bytes * share < 6 * l2_bytes()) return false;
     int bps = 0;
     if (step2_setup<MODE, S, V>(bps) != cudaSuccess) return false;
     const long long strips = (nx + t2d::TXS - 1) / t2d::TXS;
-    return strips * std::max(1, ny / 16) >= 2LL * std::max(1, sm_count()) * bps;
+    return 2 * strips * std::max(1, ny / 16) * share >= (long long)std::max(1, sm_count()) * bps;
 }
 
 template <int MODE, class S, int V>
-cudaError_t launch_step2d_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+cudaError_t launch_step2d_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t s, int share)
 {
     using L = WithMu<T2D<S>, V>;
     if (s1.nz != 1 || s1.nx < 256 || s1.ny < 16 || s1.nxp % 32 || s1.P % 32) return cudaErrorInvalidValue;
@@ -1092,11 +1099,12 @@ cudaError_t launch_step2d_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t
         if (e != cudaSuccess) return e;
     }
     // row chunks as the 3D pass's z chunks: about 40 rows, more and shorter
-    // (at least 8 rows) where that would not fill two waves
+    // (at least 8 rows) where that would not fill two waves (together with the
+    // grids stepping beside this one)
     const long long strips = (s1.nx + t2d::TXS - 1) / t2d::TXS;
     const long long cap = (long long)std::max(1, sm_count()) * bps;
     int nyc = std::max(1, (s1.ny + 20) / 40);
-    while (strips * nyc < 2 * cap && (s1.ny + nyc) / (nyc + 1) >= 8) ++nyc;
+    while (strips * nyc * share < 2 * cap && (s1.ny + nyc) / (nyc + 1) >= 8) ++nyc;
     P.zc = (s1.ny + nyc - 1) / nyc;
     const dim3 grid((unsigned)strips, (s1.ny + P.zc - 1) / P.zc, 1);
     step2d_kernel<MODE, S, V><<<grid, t2d::THREADS, L::SMEM, s>>>(P);
@@ -1104,11 +1112,11 @@ cudaError_t launch_step2d_t(const StepArgs &s1, const StepArgs &s2, cudaStream_t
 }
 
 template <class S, int V>
-cudaError_t launch_mode(int mode, const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+cudaError_t launch_mode(int mode, const StepArgs &s1, const StepArgs &s2, cudaStream_t s, int share)
 {
     switch (mode) {
-    case 0: return launch_step2d_t<0, S, V>(s1, s2, s);
-    case 1: return launch_step2d_t<1, S, V>(s1, s2, s);
+    case 0: return launch_step2d_t<0, S, V>(s1, s2, s, share);
+    case 1: return launch_step2d_t<1, S, V>(s1, s2, s, share);
     case 2: return launch_step2_t<S, V>(s1, s2, s);
     default: return cudaErrorInvalidValue;
     }
@@ -1119,32 +1127,33 @@ cudaError_t launch_mode(int mode, const StepArgs &s1, const StepArgs &s2, cudaSt
 // per update: FP32 2.86 ms in two-step passes against 2.82 ms in single
 // steps; FP16 3.02 against 1.95 ms, the two-step kernel spilling).
 template <class S>
-cudaError_t launch_variant(int mode, int variant, const StepArgs &s1, const StepArgs &s2, cudaStream_t s)
+cudaError_t launch_variant(int mode, int variant, const StepArgs &s1, const StepArgs &s2, cudaStream_t s,
+                           int share)
 {
     switch (variant) {
-    case 0: return launch_mode<S, 0>(mode, s1, s2, s);
-    case 1: return launch_mode<S, 1>(mode, s1, s2, s);
+    case 0: return launch_mode<S, 0>(mode, s1, s2, s, share);
+    case 1: return launch_mode<S, 1>(mode, s1, s2, s, share);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <class S, int V>
-bool worthwhile_mode(int mode, int nx, int ny, int nz)
+bool worthwhile_mode(int mode, int nx, int ny, int nz, int share)
 {
     switch (mode) {
-    case 0: return step2d_worthwhile_t<0, S, V>(nx, ny);
-    case 1: return step2d_worthwhile_t<1, S, V>(nx, ny);
+    case 0: return step2d_worthwhile_t<0, S, V>(nx, ny, share);
+    case 1: return step2d_worthwhile_t<1, S, V>(nx, ny, share);
     case 2: return step2_worthwhile_t<S, V>(nx, ny, nz);
     default: return false;
     }
 }
 
 template <class S>
-bool worthwhile_variant(int mode, int variant, int nx, int ny, int nz)
+bool worthwhile_variant(int mode, int variant, int nx, int ny, int nz, int share)
 {
     switch (variant) {
-    case 0: return worthwhile_mode<S, 0>(mode, nx, ny, nz);
-    case 1: return worthwhile_mode<S, 1>(mode, nx, ny, nz);
+    case 0: return worthwhile_mode<S, 0>(mode, nx, ny, nz, share);
+    case 1: return worthwhile_mode<S, 1>(mode, nx, ny, nz, share);
     default: return false;
     }
 }
@@ -1152,22 +1161,24 @@ bool worthwhile_variant(int mode, int variant, int nx, int ny, int nz)
 }  // namespace
 
 cudaError_t launch_step2(int mode, int storage, int variant, const StepArgs &s1, const StepArgs &s2,
-                         cudaStream_t s)
+                         cudaStream_t s, int share)
 {
+    share = std::max(1, share);
     switch (storage) {
-    case 0: return launch_variant<float>(mode, variant, s1, s2, s);
-    case 1: return launch_variant<__half>(mode, variant, s1, s2, s);
-    case 2: return launch_variant<__nv_bfloat16>(mode, variant, s1, s2, s);
+    case 0: return launch_variant<float>(mode, variant, s1, s2, s, share);
+    case 1: return launch_variant<__half>(mode, variant, s1, s2, s, share);
+    case 2: return launch_variant<__nv_bfloat16>(mode, variant, s1, s2, s, share);
     default: return cudaErrorInvalidValue;
     }
 }
 
-bool step2_worthwhile(int mode, int storage, int variant, int nx, int ny, int nz)
+bool step2_worthwhile(int mode, int storage, int variant, int nx, int ny, int nz, int share)
 {
+    share = std::max(1, share);
     switch (storage) {
-    case 0: return worthwhile_variant<float>(mode, variant, nx, ny, nz);
-    case 1: return worthwhile_variant<__half>(mode, variant, nx, ny, nz);
-    case 2: return worthwhile_variant<__nv_bfloat16>(mode, variant, nx, ny, nz);
+    case 0: return worthwhile_variant<float>(mode, variant, nx, ny, nz, share);
+    case 1: return worthwhile_variant<__half>(mode, variant, nx, ny, nz, share);
+    case 2: return worthwhile_variant<__nv_bfloat16>(mode, variant, nx, ny, nz, share);
     default: return false;
     }
 }
