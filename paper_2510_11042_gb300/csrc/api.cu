@@ -1,6 +1,7 @@
 // C ABI of liblbem (declared in include/lbem.h): handle life cycle, argument
 // checking, workspace layout, the step loop and the far-field call.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -48,16 +49,24 @@ struct lbem_ctx {
     bool ff_fp64 = false;       // LBEM_FAR_FIELD_FP64: 3D projection by the FP64 kernels
     int fuse = 2;               // steps per pass over the populations (lbem_set_step_fusion)
     int share = 1;              // grids stepping beside this one (the lanes of a batched run)
-    // deferred DFT of NTFF faces (see dft_flush_x_kernel)
-    float *xstage = nullptr;    // [kXStage][NC][xs_n]
+    // deferred DFT of NTFF faces (see dft_flush_x_kernel): two banks of
+    // kXBank staging slots; a full bank is summed on fstream while the steps
+    // fill the other one
+    float *xstage = nullptr;    // [2][kXBank][NC][xs_n]
     size_t xstage_floats = 0;
     long long xs_n = 0;         // cells of all faces (0: no staging)
     unsigned xs_xmask = 0;      // the x faces (staged by single steps)
     unsigned xs_allmask = 0;    // every face (staged by two-step passes)
-    int xs_cnt = 0;             // staged steps not yet summed
-    bool xs_wide = false;       // a pending step staged faces beyond x
-    unsigned xs_masks[kXStage];
-    double xs_sc[kXStage], xs_ss[kXStage];
+    int xs_bank = 0;            // the bank being filled
+    int xs_cnt = 0;             // its staged steps
+    bool xs_wide = false;       // a step staged faces beyond x that the step stream has not summed
+    unsigned xs_masks[kXBank];
+    double xs_sc[kXBank], xs_ss[kXBank];
+    cudaStream_t fstream = nullptr;           // side stream of the bank sums (3D)
+    cudaEvent_t xs_filled[2] = {nullptr, nullptr};
+    cudaEvent_t xs_summed[2] = {nullptr, nullptr};
+    bool xs_inflight[2] = {false, false};     // a sum of the bank may still run on fstream
+    int xs_last = -1;                         // bank of the last sum launched on fstream
     float *stage = nullptr;     // one FP32 plane of ncell values
     int *flag = nullptr;
     // time and source
@@ -376,6 +385,17 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->stream = (cudaStream_t)cuda_stream;
     h->err[0] = 0;
     cudaGetDevice(&h->device);
+    if (grid->mode == 2) {
+        bool ok = cudaStreamCreateWithFlags(&h->fstream, cudaStreamNonBlocking) == cudaSuccess;
+        for (int b = 0; b < 2 && ok; ++b)
+            ok = cudaEventCreateWithFlags(&h->xs_filled[b], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->xs_summed[b], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            lbem_destroy(h);
+            return fail(nullptr, LBEM_ERR_CUDA, "creating the DFT side stream failed");
+        }
+    }
     if (workspace) {
         h->ws = (char *)workspace;
         h->ws_bytes = workspace_bytes;
@@ -497,8 +517,11 @@ static void build_faces(lbem_ctx *h)
     // staging in 3D only; faces 0 and 1 are the x faces when the grid has an x extent
     h->xs_n = (h->g.mode == 2 && F.nfaces > 0) ? (long long)cells : 0;
     if ((size_t)h->xs_n * h->NC * kXStage > h->xstage_floats) h->xs_n = 0;  // cannot happen: bounded by the grid
+    // the bank sums index with 32 bits; past that the faces are summed in place
+    if ((long long)h->xs_n * h->NC * kXBank > INT_MAX || h->dft_doubles > (size_t)INT_MAX) h->xs_n = 0;
     h->xs_xmask = (F.nfaces >= 2 && F.axis[0] == 0) ? 3u : 0u;
     h->xs_allmask = (1u << F.nfaces) - 1u;
+    h->xs_bank = 0;
     h->xs_cnt = 0;
     h->xs_wide = false;
 }
@@ -697,34 +720,72 @@ int32_t lbem_set_dft_window(lbem_handle h, int64_t t_start, int32_t n_periods)
     return LBEM_OK;
 }
 
-// Sum the staged x-face DFT fields into the accumulators (dft_flush_x_kernel).
-static int flush_x_stage(lbem_ctx *h)
+// Make the step stream wait for every bank sum launched on the side stream
+// (they run in order there, so the last one covers them all).
+static int join_sums(lbem_ctx *h)
 {
-    if (h->xs_cnt == 0) return LBEM_OK;
-    DftFlushArgs f;
-    std::memset(&f, 0, sizeof f);
-    f.stage = h->xstage;
-    f.n = h->xs_n;
-    f.nc = h->NC;
-    f.cnt = h->xs_cnt;
-    f.nfaces = h->faces.nfaces;
-    f.dft = h->dft;
-    for (int k = 0; k < h->faces.nfaces; ++k) {
-        f.start[k] = h->faces.cell_start[k];
-        f.plane[k] = (long long)h->faces.nu[k] * h->faces.nv[k];
-        f.face_off[k] = h->faces.off[k];
+    if (h->xs_last < 0) return LBEM_OK;
+    const int b = h->xs_last;
+    h->xs_last = -1;
+    h->xs_inflight[0] = h->xs_inflight[1] = false;
+    CK(h, cudaStreamWaitEvent(h->stream, h->xs_summed[b], 0));
+    return LBEM_OK;
+}
+
+// Sum the bank being filled into the DFT accumulators (dft_flush_x_kernel) and
+// fill the other bank next.  beside: on the side stream, after the steps that
+// filled the bank and beside the steps that follow (a small grid that shares
+// the SMs with them); else on the step stream after every earlier sum, with a
+// full grid, leaving the DFT complete on the step stream.
+static int flush_x_stage(lbem_ctx *h, bool beside)
+{
+    if (!beside) {
+        const int rc = join_sums(h);
+        if (rc != LBEM_OK) return rc;
     }
-    f.start[h->faces.nfaces] = h->faces.cell_start[h->faces.nfaces];
-    for (int s = 0; s < h->xs_cnt; ++s) {
-        f.mask[s] = h->xs_masks[s];
-        f.sc[s] = h->xs_sc[s];
-        f.ss[s] = h->xs_ss[s];
+    const int b = h->xs_bank;
+    if (h->xs_cnt > 0) {
+        DftFlushArgs f;
+        std::memset(&f, 0, sizeof f);
+        f.stage = h->xstage + (size_t)b * kXBank * h->NC * h->xs_n;
+        f.n = h->xs_n;
+        f.nc = h->NC;
+        f.cnt = h->xs_cnt;
+        f.nfaces = h->faces.nfaces;
+        f.dft = h->dft;
+        for (int k = 0; k < h->faces.nfaces; ++k) {
+            f.start[k] = h->faces.cell_start[k];
+            f.plane[k] = (long long)h->faces.nu[k] * h->faces.nv[k];
+            f.face_off[k] = h->faces.off[k];
+        }
+        f.start[h->faces.nfaces] = h->faces.cell_start[h->faces.nfaces];
+        for (int s = 0; s < h->xs_cnt; ++s) {
+            f.mask[s] = h->xs_masks[s];
+            f.sc[s] = h->xs_sc[s];
+            f.ss[s] = h->xs_ss[s];
+        }
+        h->xs_cnt = 0;
+        if (beside) {
+            CK(h, cudaEventRecord(h->xs_filled[b], h->stream));
+            CK(h, cudaStreamWaitEvent(h->fstream, h->xs_filled[b], 0));
+            cudaError_t e = launch_dft_flush_x(f, h->fstream, sm_count());
+            if (e != cudaSuccess) return cuda_fail(h, e, "DFT bank sum launch");
+            CK(h, cudaEventRecord(h->xs_summed[b], h->fstream));
+            h->xs_inflight[b] = true;
+            h->xs_last = b;
+        } else {
+            cudaError_t e = launch_dft_flush_x(f, h->stream, 0);
+            if (e != cudaSuccess) return cuda_fail(h, e, "DFT bank sum launch");
+        }
+        h->launches += 1;
+        h->xs_bank = b ^ 1;
+        // the steps that fill the other bank start after its last sum read it
+        if (h->xs_inflight[b ^ 1]) {
+            h->xs_inflight[b ^ 1] = false;
+            CK(h, cudaStreamWaitEvent(h->stream, h->xs_summed[b ^ 1], 0));
+        }
     }
-    h->xs_cnt = 0;
-    h->xs_wide = false;
-    cudaError_t e = launch_dft_flush_x(f, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "x-face DFT flush launch");
-    h->launches += 1;
+    if (!beside) h->xs_wide = false;
     return LBEM_OK;
 }
 
@@ -774,7 +835,7 @@ static void step_args_at(lbem_ctx *h, StepArgs &a, int64_t tn, int in, int out)
 static void stage_slot(lbem_ctx *h, StepArgs &a, unsigned mask)
 {
     if (!a.dft_on || h->xs_n == 0 || mask == 0) return;
-    a.xstage = h->xstage + (size_t)h->xs_cnt * h->NC * h->xs_n;
+    a.xstage = h->xstage + ((size_t)h->xs_bank * kXBank + h->xs_cnt) * h->NC * h->xs_n;
     a.xs_n = h->xs_n;
     for (int f = 0; f < h->faces.nfaces; ++f) a.xs_start[f] = h->faces.cell_start[f];
     h->xs_masks[h->xs_cnt] = mask;
@@ -796,10 +857,10 @@ static bool two_step_passes(lbem_ctx *h)
            step2_worthwhile(h->g.mode, h->g.storage, step_variant(h), h->g.nx, h->g.ny, h->g.nz, h->share);
 }
 
-int32_t lbem_step(lbem_handle h, int64_t n)
+// The steps of lbem_step; on an error the step stream is still joined with
+// the side stream's sums, so later work on it sees a consistent DFT.
+static int step_loop(lbem_ctx *h, int64_t n)
 {
-    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
-    if (n < 0) return fail(h, LBEM_ERR_ARG, "n must be >= 0");
     StepArgs a;
     fill_common_args(h, a);
     const bool pairs = two_step_passes(h);
@@ -808,8 +869,8 @@ int32_t lbem_step(lbem_handle h, int64_t n)
     for (int64_t k = 0; k < n;) {
         if (pairs && n - k >= 2) {
             // two steps in one pass: level n from f[cur], level n+2 into f[cur ^ 1]
-            if (h->xs_cnt + 2 > kXStage) {
-                const int rc = flush_x_stage(h);
+            if (h->xs_cnt + 2 > kXBank) {
+                const int rc = flush_x_stage(h, true);
                 if (rc != LBEM_OK) return rc;
             }
             step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
@@ -828,9 +889,10 @@ int32_t lbem_step(lbem_handle h, int64_t n)
             k += 2;
         } else {
             // a single step updates the faces it does not stage in place, so
-            // terms staged for them by two-step passes go in first
+            // terms staged for them by two-step passes go in first, on the
+            // step stream
             if (h->xs_wide) {
-                const int rc = flush_x_stage(h);
+                const int rc = flush_x_stage(h, false);
                 if (rc != LBEM_OK) return rc;
             }
             step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
@@ -848,12 +910,25 @@ int32_t lbem_step(lbem_handle h, int64_t n)
             h->t += 1;
             k += 1;
         }
-        if (h->xs_cnt == kXStage) {
-            const int rc = flush_x_stage(h);
+        if (h->xs_cnt == kXBank) {
+            const int rc = flush_x_stage(h, true);
             if (rc != LBEM_OK) return rc;
         }
     }
-    return flush_x_stage(h);  // every call leaves the DFT complete
+    return flush_x_stage(h, false);  // every call leaves the DFT complete on the step stream
+}
+
+int32_t lbem_step(lbem_handle h, int64_t n)
+{
+    if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (n < 0) return fail(h, LBEM_ERR_ARG, "n must be >= 0");
+    const int rc = step_loop(h, n);
+    if (rc != LBEM_OK && h->xs_last >= 0) {
+        cudaStreamWaitEvent(h->stream, h->xs_summed[h->xs_last], 0);
+        h->xs_last = -1;
+        h->xs_inflight[0] = h->xs_inflight[1] = false;
+    }
+    return rc;
 }
 
 int32_t lbem_set_step_fusion(lbem_handle h, int32_t steps_per_pass)
@@ -1631,7 +1706,13 @@ int32_t lbem_sync(lbem_handle h)
 void lbem_destroy(lbem_handle h)
 {
     if (!h) return;
+    if (h->fstream) cudaStreamSynchronize(h->fstream);
     if ((h->owns_ws && h->ws) || (h->adj_owns && h->adj_ws)) cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b) {
+        if (h->xs_filled[b]) cudaEventDestroy(h->xs_filled[b]);
+        if (h->xs_summed[b]) cudaEventDestroy(h->xs_summed[b]);
+    }
+    if (h->fstream) cudaStreamDestroy(h->fstream);
     if (h->owns_ws && h->ws) cudaFree(h->ws);
     if (h->adj_owns && h->adj_ws) cudaFree(h->adj_ws);
     delete h;

@@ -315,10 +315,12 @@ struct FaceGeom {
     int lo[3], hi[3];
 };
 
-// Deferred DFT of NTFF faces: kXStage steps of staged fields [step][NC][n]
-// (n the cells of all faces, face f from start[f]), the faces each step
-// staged, and the steps' phase coefficients.
-constexpr int kXStage = 16;
+// Deferred DFT of NTFF faces: two banks of kXBank steps of staged fields
+// [step][NC][n] (n the cells of all faces, face f from start[f]); one flush
+// sums one bank: the faces each of its steps staged and the steps' phase
+// coefficients.
+constexpr int kXBank = 8;
+constexpr int kXStage = 2 * kXBank;
 struct DftFlushArgs {
     const float *stage;
     long long n;
@@ -327,10 +329,12 @@ struct DftFlushArgs {
     long long start[kMaxFaces + 1];
     long long plane[kMaxFaces];     // nu * nv of each face
     long long face_off[kMaxFaces];
-    unsigned mask[kXStage];
-    double sc[kXStage], ss[kXStage];
+    unsigned mask[kXBank];
+    double sc[kXBank], ss[kXBank];
 };
-cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s);
+// blocks = 0: one thread per summed value; blocks > 0: that many blocks
+// (grid-stride), small enough to sit beside a running step kernel.
+cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s, int blocks);
 
 struct FarFieldArgs {
     const double *dft;

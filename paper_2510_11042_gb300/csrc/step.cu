@@ -50,6 +50,7 @@
 // memory-bound stencil (~1 flop/byte), so it runs on the CUDA cores; no
 // tensor-core path applies.
 #include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "step_cell.cuh"
@@ -264,31 +265,53 @@ __global__ void line_init_kernel(const StepArgs a)
 
 
 // Sums cnt staged steps of face fields into the FP64 DFT accumulators in step
-// order, with the same fma as the direct path: one thread per (face cell,
-// component), reads coalesced along the cells.  Slot s holds the faces in
-// mask[s].
-__global__ void dft_flush_x_kernel(const DftFlushArgs a)
+// order, with the same fma as the direct path.  A thread takes one face cell
+// per pass of the grid-stride loop and the components k = blockIdx.y,
+// blockIdx.y + gridDim.y, ...; reads are coalesced along the cells and a
+// component's staged values are all loaded before its FP64 chain.  Slot s
+// holds the faces in mask[s].  A small grid of it (one block per SM, every
+// component) runs beside the two-step kernel that fills the other bank, one
+// block beside each two-step block: that needs its warps to fit the
+// registers the two-step block leaves on each SM sub-partition (1024 beside
+// the 19 warps of 96 registers of the 16-bit kernel, hence at most 32
+// registers a thread) and an SM shared-memory configuration that still holds
+// a two-step block (the maximum carveout: a flush block that lands first on
+// an idle SM would otherwise configure it for L1 and keep the next two-step
+// block off that SM while it runs).
+constexpr int kFlushThreads = 128;
+__global__ void __launch_bounds__(kFlushThreads, 16) dft_flush_x_kernel(const DftFlushArgs a)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n * a.nc) return;
-    const long long j = i % a.n;
-    const int k = (int)(i / a.n);
-    int f = 0;
-    while (f + 1 < a.nfaces && j >= a.start[f + 1]) ++f;
-    unsigned any = 0;
-    for (int s = 0; s < a.cnt; ++s) any |= (a.mask[s] >> f) & 1u;
-    if (!any) return;
-    const long long r = j - a.start[f];
-    double *base = a.dft + a.face_off[f] + r;
-    double re = base[(2 * k + 0) * a.plane[f]], im = base[(2 * k + 1) * a.plane[f]];
-    for (int s = 0; s < a.cnt; ++s) {
-        if (!((a.mask[s] >> f) & 1u)) continue;
-        const double v = (double)a.stage[((long long)s * a.nc + k) * a.n + j];
-        re = fma(v, a.sc[s], re);
-        im = fma(v, -a.ss[s], im);
+    // 32-bit offsets: the launcher checks that kXBank staged steps and the
+    // accumulators of every face stay below 2^31 elements
+    const int n = (int)a.n;
+    const int slot = a.nc * n;  // floats of one staged step
+    for (int j = blockIdx.x * kFlushThreads + threadIdx.x; j < n; j += gridDim.x * kFlushThreads) {
+        int f = 0;
+        while (f + 1 < a.nfaces && j >= a.start[f + 1]) ++f;
+        unsigned on = 0;  // the slots that staged face f
+#pragma unroll
+        for (int s = 0; s < kXBank; ++s)
+            if (s < a.cnt) on |= ((a.mask[s] >> f) & 1u) << s;
+        if (!on) continue;
+        const float *src = a.stage + j;
+        double *base = a.dft + a.face_off[f] + (j - (int)a.start[f]);
+        const int plane = (int)a.plane[f];
+        for (int k = blockIdx.y; k < a.nc; k += gridDim.y) {
+            float v[kXBank];
+#pragma unroll
+            for (int s = 0; s < kXBank; ++s)
+                v[s] = ((on >> s) & 1u) ? src[s * slot + k * n] : 0.f;
+            double re = base[(2 * k + 0) * plane], im = base[(2 * k + 1) * plane];
+#pragma unroll
+            for (int s = 0; s < kXBank; ++s) {
+                if (!((on >> s) & 1u)) continue;
+                re = fma((double)v[s], a.sc[s], re);
+                im = fma((double)v[s], -a.ss[s], im);
+            }
+            base[(2 * k + 0) * plane] = re;
+            base[(2 * k + 1) * plane] = im;
+        }
     }
-    base[(2 * k + 0) * a.plane[f]] = re;
-    base[(2 * k + 1) * a.plane[f]] = im;
 }
 
 template <int MODE, class S, bool REC = false, bool MU = false, bool ANA = false>
@@ -400,11 +423,31 @@ int batch_max_blocks_per_sm(int mode, int storage)
     }
 }
 
-cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s)
+cudaError_t launch_dft_flush_x(const DftFlushArgs &a, cudaStream_t s, int blocks)
 {
-    if (a.cnt < 1 || a.cnt > kXStage || a.n <= 0) return cudaErrorInvalidValue;
-    const long long total = a.n * a.nc;
-    dft_flush_x_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a);
+    if (a.cnt < 1 || a.cnt > kXBank || a.n <= 0 || blocks < 0) return cudaErrorInvalidValue;
+    if ((long long)kXBank * a.nc * a.n > INT_MAX) return cudaErrorInvalidValue;
+    for (int f = 0; f < a.nfaces; ++f)
+        if (a.face_off[f] + 2LL * a.nc * a.plane[f] > INT_MAX) return cudaErrorInvalidValue;
+    const long long need = (a.n + kFlushThreads - 1) / kFlushThreads;
+    const dim3 grid(blocks > 0 ? (unsigned)std::min<long long>(blocks, need) : (unsigned)need,
+                    blocks > 0 ? 1u : (unsigned)a.nc);
+    {
+        static std::mutex mu;
+        static bool carved[kMaxDevices];
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!carved[dev]) {
+            e = cudaFuncSetAttribute(dft_flush_x_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+            if (e != cudaSuccess) return e;
+            carved[dev] = true;
+        }
+    }
+    dft_flush_x_kernel<<<grid, kFlushThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -352,10 +352,11 @@ def test_storage_scale_and_checkpoint_in_grouped_16bit_layout(storage):
 
 @pytest.mark.parametrize("mode", ["ez", "3d"])
 def test_dft_same_for_any_step_split(mode):
-    """The x faces' DFT terms are staged and summed in 16-step batches and at
-    the end of every lbem_step call, in the same order and with the same fma
-    as the other faces: one call for the whole run and one call per step give
-    the same accumulators bit for bit, and they match the FP64 oracle."""
+    """The x faces' DFT terms are staged in banks of 8 steps, each summed on a
+    side stream beside the steps that fill the other bank, and at the end of
+    every lbem_step call, in the same order and with the same fma as the
+    other faces: one call for the whole run and one call per step give the
+    same accumulators bit for bit, and they match the FP64 oracle."""
     if mode == "ez":
         p = W.cylinder_problem(n=72, x=3.0, wavelength=10.0, eps_in=2.25, w=6, mode="ez", periods=8)
     else:
