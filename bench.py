@@ -292,6 +292,7 @@ def run_gpu(args, rank, world, local_rank):
     main = one_storage("f32", K, Wm, True)
     probe_2d = None if (args.no_batch or world > 1) else run_probe_2d(dev)
     variants_3d = None if (args.no_batch or world > 1) else run_variants_3d(dev)
+    in_place = None if (args.no_batch or world > 1) else run_in_place(dev, n=args.size)
     batched = None if (args.no_batch or world > 1) else run_batched(dev)
     adjoint = None if (args.no_adjoint or world > 1) else run_adjoint(dev)
     secondary = {}
@@ -366,6 +367,8 @@ def run_gpu(args, rank, world, local_rank):
         line["bandwidth_probe_2d"] = probe_2d
     if variants_3d:
         line["kernel_variants_3d"] = variants_3d
+    if in_place:
+        line["in_place_streaming"] = in_place
     if batched:
         line["batched"] = batched
     if adjoint:
@@ -580,6 +583,55 @@ def run_variants_3d(dev, updates=44, storages=("f32", "f16"), n=384):
     return out
 
 
+def run_in_place(dev, updates=40, storages=("f32", "f16", "bf16"), n=384):
+    """In-place streaming (one population buffer) on the sphere against the
+    two-buffer single step it is bitwise equal to, both with the DFT window on,
+    over an even number of updates (push and in-place steps alternate): CUDA
+    event time per update, the B_cell byte model's bandwidth, and the
+    workspace each scheme needs."""
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    p = W.sphere_problem(n=n)
+    cells = int(np.prod(p.shape))
+    hbm, _ = peaks()
+    out = {"workload": f"sphere {n}^3" + (" (the bench workload)" if n == 384 else ""),
+           "updates_timed": updates}
+
+    def timed(st, streaming):
+        s = lbem.Solver(p.shape, p.eps, "3d", st, p.absorber_width, p.sigma_max, device=dev, streaming=streaming)
+        s.set_step_fusion(1)
+        s.inject(p.wave)
+        s.step(6)
+        s.set_dft_window(s.time + 1, 1)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(s.stream)
+        s.step(updates)
+        ev[1].record(s.stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / updates
+        ws = int(s.workspace.numel())
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        return ms, ws
+
+    for st in storages:
+        bc = b_cell("3d", st)
+        rec = {}
+        for streaming in ("in_place", "two_buffers"):
+            ms, ws = timed(st, streaming)
+            gbs = bc * cells / (ms / 1e3) / 1e9
+            rec[streaming] = {"kernel_ms": round(ms, 4), "mlups": round(cells / (ms / 1e3) / 1e6, 1),
+                              "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1),
+                              "hbm_frac": round(gbs / hbm, 4), "workspace_gb": round(ws / 1e9, 3)}
+        entry = dict(rec["in_place"], two_buffers_single_step=rec["two_buffers"])
+        entry["time_vs_two_buffers"] = round(rec["in_place"]["kernel_ms"] / rec["two_buffers"]["kernel_ms"], 3)
+        entry["workspace_vs_two_buffers"] = round(rec["in_place"]["workspace_gb"] / rec["two_buffers"]["workspace_gb"], 3)
+        out[st] = entry
+    return out
+
+
 # ------------------------------------------------------------------ adjoint workload
 def run_adjoint(dev, K=200):
     """Permittivity gradient of |S(theta)|^2 at theta = 0, 45, 90 degrees on the
@@ -779,8 +831,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-updates", type=float, default=2)
-    ap.add_argument("--section", default="all", choices=["all", "adjoint_probe", "probe_2d", "variants_3d"],
-                    help="adjoint_probe / probe_2d / variants_3d: only that measurement (profiling)")
+    ap.add_argument("--section", default="all",
+                    choices=["all", "adjoint_probe", "probe_2d", "variants_3d", "in_place"],
+                    help="adjoint_probe / probe_2d / variants_3d / in_place: only that measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -790,13 +843,15 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.section in ("adjoint_probe", "probe_2d", "variants_3d"):
+    if args.section in ("adjoint_probe", "probe_2d", "variants_3d", "in_place"):
         import torch
         from paper_2510_11042_gb300 import build as lib_build
         lib_build.build()
         dev = torch.device("cuda", local_rank)
         if args.section == "variants_3d":
             out = run_variants_3d(dev, n=args.size)
+        elif args.section == "in_place":
+            out = run_in_place(dev, n=args.size)
         else:
             out = {"adjoint_probe": _adjoint_probe_3d, "probe_2d": run_probe_2d}[args.section](dev)
         print(json.dumps(out), flush=True)

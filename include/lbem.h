@@ -90,7 +90,25 @@ typedef struct {
     double sigma_max;
     int32_t storage;    /* lbem_storage */
     int32_t mode;       /* lbem_mode */
+    int32_t streaming;  /* lbem_streaming (0: two buffers) */
 } lbem_grid_desc;
+
+/* How the populations stream between steps (the pull step of Sec. 2.1 with
+ * the Eq. 4 clamp in either case; the same populations bit for bit):
+ *  LBEM_STREAM_TWO_BUFFERS: read one population buffer, write the other; the
+ *    default, and the only scheme with two-step passes (lbem_set_step_fusion),
+ *    batched runs and the adjoint.
+ *  LBEM_STREAM_IN_PLACE: one buffer (half the population memory, so larger
+ *    grids fit) updated in place by alternating a step that pushes each
+ *    post-collision population into its downstream neighbour's opposite slot
+ *    and a step that reads and writes only the cell's own slots (the "AA"
+ *    pattern), with two thin face buffers per axis for the clamped faces.
+ *    Single steps only.  The state is in its ordinary layout after an even
+ *    number of steps; calls that read or set populations or fields after an
+ *    odd number first rearrange it (one pass over the populations).
+ *    lbem_batch_create, lbem_forward_checkpointed and lbem_adjoint refuse such
+ *    handles with LBEM_ERR_ARG. */
+typedef enum { LBEM_STREAM_TWO_BUFFERS = 0, LBEM_STREAM_IN_PLACE = 1 } lbem_streaming;
 
 /* A linearly polarised incident plane wave (Sec. 2.3: "the incident field
  * considered in this work is linearly polarized").  dir must be +x or +y for
@@ -136,8 +154,9 @@ typedef struct {
     double origin[3];      /* analytic source: where tau = n */
 } lbem_plane_wave;
 
-/* Bytes of device workspace a grid needs (populations in two buffers, the
- * permittivity map, the incident line, the DFT accumulators and scratch). */
+/* Bytes of device workspace a grid needs (populations in two buffers, or one
+ * with the face buffers of in-place streaming, the permittivity map, the
+ * incident line, the DFT accumulators and scratch). */
 int32_t lbem_workspace_bytes(const lbem_grid_desc *grid, size_t *bytes_out);
 
 /* Create a solver on the current device.
@@ -211,9 +230,11 @@ int32_t lbem_far_field(lbem_handle h, const double *theta_host, const double *ph
  * planes; 2D: 128-cell strips marching along y) plus its edge halos in shared
  * memory, bitwise the same result as two single steps (16-bit storage rounds
  * the intermediate state as a single step stores it).  It is taken where its
- * blocks fill the GPU (one wave of resident blocks in 3D, two in 2D, where
- * smaller grids sit in L2); other grids, the closed-form source (bound by its
- * wave evaluations, not by memory) and a last odd step take single steps.
+ * blocks fill the GPU (one wave of resident blocks in 3D, two in 2D) and, in
+ * 2D, where the population buffers of the grids stepping together outgrow
+ * the L2 cache (smaller grids are served from it); other grids, the
+ * closed-form source (bound by its wave evaluations, not by memory), a last
+ * odd step and handles with in-place streaming take single steps.
  * 1 always takes single steps.  Anything else: LBEM_ERR_ARG. */
 int32_t lbem_set_step_fusion(lbem_handle h, int32_t steps_per_pass);
 

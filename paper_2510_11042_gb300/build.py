@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbem.so")
-SOURCES = ["step.cu", "step2.cu", "observe.cu", "api.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["step.cu", "step2.cu", "aa.cu", "observe.cu", "api.cu", "noalloc.cu", "adjoint.cu"]
 HEADERS = [os.path.join(CSRC, "lbem_internal.cuh"), os.path.join(CSRC, "step_cell.cuh"),
            os.path.join(ROOT, "include", "lbem.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

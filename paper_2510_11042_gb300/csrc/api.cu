@@ -48,6 +48,11 @@ struct lbem_ctx {
     size_t x32_cap = 0, tab32_cap = 0;
     bool ff_fp64 = false;       // LBEM_FAR_FIELD_FP64: 3D projection by the FP64 kernels
     int fuse = 2;               // steps per pass over the populations (lbem_set_step_fusion)
+    // in-place streaming (LBEM_STREAM_IN_PLACE): f[0] only, the face buffers
+    bool aa = false;
+    int aa_phase = 0;           // 0: canonical state, 1: streamed (after a push step)
+    bool aa_fi_valid = false;   // aa_g.fi holds the clamped values of the canonical state
+    AaArgs aa_g;
     int share = 1;              // grids stepping beside this one (the lanes of a batched run)
     // deferred DFT of NTFF faces (see dft_flush_x_kernel): two banks of
     // kXBank staging slots; a full bank is summed on fstream while the steps
@@ -131,12 +136,33 @@ static int check_status(lbem_ctx *h)
     return LBEM_OK;
 }
 
+// In-place streaming: bring the state to the canonical layout (after a push
+// step it is the streamed one) before anything reads or writes populations.
+static int aa_settle(lbem_ctx *h)
+{
+    if (!h->aa || h->aa_phase == 0) return LBEM_OK;
+    CK(h, launch_aa_canonical(h->g.mode, h->g.storage, h->f[0], h->P, h->g.nx, h->g.ny, h->g.nz, h->nxp, h->aa_g,
+                              h->stream));
+    h->launches += 3;
+    h->aa_phase = 0;
+    h->aa_fi_valid = false;
+    return LBEM_OK;
+}
+
+#define AA_SETTLE(h)                           \
+    do {                                       \
+        const int rc_ = aa_settle(h);          \
+        if (rc_ != LBEM_OK) return rc_;        \
+    } while (0)
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t f0, f1, inv_eps, inv_mu, pw_tab, line0, line1, line2, dft, line_dft, scratch, ff32, stage, flag, total;
     size_t x32_cap, tab32_cap;  // float2 capacities of the 3D FP32 far field (0 in 2D)
     size_t xstage, xstage_floats;  // staged face DFT fields
+    size_t aa_faces;               // in-place streaming: FI and FO of the six directions
+    long long fplane[3];           // face cells of each axis (0 along 1-cell axes)
     int Q, nxp, n_line_max;
     long long P, ncell;
     size_t elem, dft_doubles_max, scratch_doubles;
@@ -149,6 +175,8 @@ static int check_grid(const lbem_grid_desc *g, char *why, size_t n)
         return snprintf(why, n, "grid extents must be >= 1 (got %d x %d x %d)", g->nx, g->ny, g->nz), 0;
     if (g->mode < 0 || g->mode > 2) return snprintf(why, n, "unknown mode %d", g->mode), 0;
     if (g->storage < 0 || g->storage > 2) return snprintf(why, n, "unknown storage %d", g->storage), 0;
+    if (g->streaming != LBEM_STREAM_TWO_BUFFERS && g->streaming != LBEM_STREAM_IN_PLACE)
+        return snprintf(why, n, "unknown streaming %d", g->streaming), 0;
     if (g->mode != 2 && g->nz != 1)
         return snprintf(why, n, "the 2D modes (EZ, HZ) need nz == 1"), 0;
     if (g->mode == 2 && g->nz < 2) return snprintf(why, n, "3D mode needs nz >= 2"), 0;
@@ -182,8 +210,17 @@ static Layout make_layout(const lbem_grid_desc *g)
     L.scratch_doubles = (size_t)kAngleBatch * kMaxChunks * 12 + kAngleBatch * 16;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    const bool aa = g->streaming == LBEM_STREAM_IN_PLACE;
     L.f0 = take((size_t)L.Q * L.P * L.elem);
-    L.f1 = take((size_t)L.Q * L.P * L.elem);
+    L.f1 = aa ? 0 : take((size_t)L.Q * L.P * L.elem);
+    const long long n3[3] = {g->nx, g->ny, g->nz};
+    size_t face_bytes = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        L.fplane[ax] = (aa && n3[ax] > 1) ? L.ncell / n3[ax] : 0;
+        // FI and FO of both directions, each 256-byte aligned for vector access
+        if (L.fplane[ax]) face_bytes += 4 * align256((size_t)L.fplane[ax] * NC * L.elem);
+    }
+    L.aa_faces = take(face_bytes);
     L.inv_eps = take((size_t)L.P * 4);
     L.inv_mu = take((size_t)L.P * 4);
     L.pw_tab = take((size_t)(g->nx + g->ny + g->nz) * 12);
@@ -403,15 +440,30 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
         cudaError_t e = cudaMalloc((void **)&h->ws, L.total);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            delete h;
+            h->ws = nullptr;
+            lbem_destroy(h);
             return fail(nullptr, LBEM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", L.total,
                         cudaGetErrorString(e));
         }
         h->owns_ws = true;
         h->ws_bytes = L.total;
     }
+    h->aa = grid->streaming == LBEM_STREAM_IN_PLACE;
     h->f[0] = h->ws + L.f0;
-    h->f[1] = h->ws + L.f1;
+    h->f[1] = h->aa ? nullptr : h->ws + L.f1;
+    std::memset(&h->aa_g, 0, sizeof h->aa_g);
+    if (h->aa) {
+        // FI then FO, each direction i = 1..6 on its axis: NC face planes
+        char *p = h->ws + L.aa_faces;
+        for (int ax = 0; ax < 3; ++ax) h->aa_g.fplane[ax] = L.fplane[ax];
+        for (int k = 0; k < 2; ++k)
+            for (int i = 1; i < 7; ++i) {
+                const long long plane = L.fplane[(i - 1) / 2];
+                if (plane == 0) continue;
+                (k == 0 ? h->aa_g.fi : h->aa_g.fo)[i] = p;
+                p += align256((size_t)plane * h->NC * L.elem);
+            }
+    }
     h->inv_eps = (float *)(h->ws + L.inv_eps);
     h->inv_mu = (float *)(h->ws + L.inv_mu);
     h->pw_ph = (float2 *)(h->ws + L.pw_tab);
@@ -437,7 +489,7 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     int rc = LBEM_OK;
     cudaError_t e = cudaMemsetAsync(h->flag, 0, 256, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, (size_t)L.Q * L.P * L.elem, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, (size_t)L.Q * L.P * L.elem, h->stream);
+    if (e == cudaSuccess && h->f[1]) e = cudaMemsetAsync(h->f[1], 0, (size_t)L.Q * L.P * L.elem, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->inv_eps, 0, (size_t)L.P * 4, h->stream);
     if (e == cudaSuccess) e = launch_fill(h->inv_mu, L.P, 1.0f, h->stream);
     if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaMemsetAsync");
@@ -572,6 +624,8 @@ int32_t lbem_inject_plane_wave(lbem_handle h, const lbem_plane_wave *w)
         return fail(h, LBEM_ERR_ARG, "source_index must lie upstream of the total-field box");
     if (h->has_wave) {
         // the stored state holds scattered parts inside the old box: make it total again
+        AA_SETTLE(h);
+        h->aa_fi_valid = false;
         CK(h, launch_add_incident(h->g.mode, h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx, h->g.ny,
                                   h->g.nz, h->nxp, inc_view(h), 1.0f, h->stream));
         h->launches += 1;
@@ -646,6 +700,8 @@ static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w)
                         "axis %d: an NTFF box needs W <= ntff_lo < tfsf_lo <= tfsf_hi < ntff_hi <= n-1-W", a);
     }
     if (h->has_wave) {
+        AA_SETTLE(h);
+        h->aa_fi_valid = false;
         CK(h, launch_add_incident(h->g.mode, h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx,
                                   h->g.ny, h->g.nz, h->nxp, inc_view(h), 1.0f, h->stream));
         h->launches += 1;
@@ -701,6 +757,8 @@ static int inject_analytic(lbem_ctx *h, const lbem_plane_wave *w)
     h->dft_periods = 0;
     if (h->dft_doubles) CK(h, cudaMemsetAsync(h->dft, 0, h->dft_doubles * 8, h->stream));
     // the stored state holds scattered parts inside the new box
+    AA_SETTLE(h);
+    h->aa_fi_valid = false;
     CK(h, launch_add_incident(h->g.mode, h->g.storage, h->f[h->cur], h->P, h->Q, h->scale, h->g.nx, h->g.ny,
                               h->g.nz, h->nxp, inc_view(h), -1.0f, h->stream));
     h->launches += 1;
@@ -845,6 +903,24 @@ static void stage_slot(lbem_ctx *h, StepArgs &a, unsigned mask)
     ++h->xs_cnt;
 }
 
+// In-place streaming: aim the push step's writes (kind 0, through fout_q) or
+// the in-place step's reads (kind 1, through fin_q) of direction i at slot
+// opp(i) of the single buffer.
+static void aa_aim(lbem_ctx *h, StepArgs &a, int kind)
+{
+    const size_t plane_bytes = (size_t)h->P * h->elem;
+    for (int i = 0; i < 7; ++i) {
+        const int o = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+        for (int s = 0; s < h->NC; ++s) {
+            char *p = (char *)h->f[0] + (size_t)(o * h->NC + s) * plane_bytes;
+            if (kind == 0)
+                a.fout_q[i * h->NC + s] = p;
+            else
+                a.fin_q[i * h->NC + s] = p;
+        }
+    }
+}
+
 // The kernel variant of the update: 0 plain, 1 with the mu_r map, 2 with the
 // closed-form source.
 static int step_variant(const lbem_ctx *h) { return h->analytic ? 2 : (h->mu_on ? 1 : 0); }
@@ -853,7 +929,7 @@ static int step_variant(const lbem_ctx *h) { return h->analytic ? 2 : (h->mu_on 
 // blocks fill the GPU.
 static bool two_step_passes(lbem_ctx *h)
 {
-    return h->fuse == 2 &&
+    return h->fuse == 2 && !h->aa &&
            step2_worthwhile(h->g.mode, h->g.storage, step_variant(h), h->g.nx, h->g.ny, h->g.nz, h->share);
 }
 
@@ -895,18 +971,37 @@ static int step_loop(lbem_ctx *h, int64_t n)
                 const int rc = flush_x_stage(h, false);
                 if (rc != LBEM_OK) return rc;
             }
-            step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
+            const int kind = h->aa_phase;  // in-place streaming: 0 push, 1 in place
+            if (h->aa && kind == 0 && !h->aa_fi_valid) {
+                CK(h, launch_aa_fill(h->g.mode, h->g.storage, h->f[0], h->P, h->g.nx, h->g.ny, h->g.nz, h->nxp,
+                                     h->aa_g, h->stream));
+                h->launches += 1;
+                h->aa_fi_valid = true;
+            }
+            if (h->aa) {
+                step_args_at(h, a, h->t, 0, 0);
+                aa_aim(h, a, kind);
+            } else {
+                step_args_at(h, a, h->t, h->cur, h->cur ^ 1);
+            }
             const int cnt0 = h->xs_cnt;
             stage_slot(h, a, h->xs_xmask);
-            cudaError_t e = h->analytic ? launch_step_analytic(h->g.mode, h->g.storage, a, h->stream)
-                            : h->mu_on  ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
-                                        : launch_step(h->g.mode, h->g.storage, a, h->stream);
+            cudaError_t e = h->aa       ? launch_aa_step(h->g.mode, h->g.storage, step_variant(h), kind, a,
+                                                         h->aa_g, h->stream)
+                            : h->analytic ? launch_step_analytic(h->g.mode, h->g.storage, a, h->stream)
+                            : h->mu_on    ? launch_step_mu(h->g.mode, h->g.storage, a, h->stream)
+                                          : launch_step(h->g.mode, h->g.storage, a, h->stream);
             if (e != cudaSuccess) {
                 h->xs_cnt = cnt0;
                 return cuda_fail(h, e, "step kernel launch");
             }
             h->launches += 1;
-            h->cur ^= 1;
+            if (h->aa) {
+                h->aa_phase ^= 1;
+                h->aa_fi_valid = kind == 1;  // the in-place step rewrote them; a push step used them up
+            } else {
+                h->cur ^= 1;
+            }
             h->t += 1;
             k += 1;
         }
@@ -1004,6 +1099,8 @@ extern "C" int32_t lbem_batch_create(const lbem_handle *handles, int32_t count, 
             return bfail(nullptr, LBEM_ERR_ARG, "batched runs support mu_r = 1 only");
         if (handles[i]->analytic)
             return bfail(nullptr, LBEM_ERR_ARG, "batched runs need the incident-line source");
+        if (handles[i]->aa)
+            return bfail(nullptr, LBEM_ERR_ARG, "batched runs need two population buffers (not in-place streaming)");
         if (handles[i]->device != dev) return bfail(nullptr, LBEM_ERR_ARG, "handle %d is on another device", i);
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return bfail(nullptr, LBEM_ERR_ARG, "handle %d repeated", i);
@@ -1479,6 +1576,7 @@ int32_t lbem_get_populations(lbem_handle h, float *out, int32_t on_device)
     if (!h || !out) return fail(h, LBEM_ERR_ARG, "NULL argument");
     for (int q = 0; q < h->Q; ++q) {
         float *dst = on_device ? out + (size_t)q * h->ncell : h->stage;
+        AA_SETTLE(h);
         CK(h, launch_pack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, h->scale, dst, h->g.nx, h->g.ny,
                           h->g.nz, h->nxp, inc_view(h), h->stream));
         h->launches += 1;
@@ -1500,6 +1598,8 @@ int32_t lbem_set_populations(lbem_handle h, const float *in, int32_t on_device)
             CK(h, cudaMemcpyAsync(h->stage, src, (size_t)h->ncell * 4, cudaMemcpyHostToDevice, h->stream));
             src = h->stage;
         }
+        AA_SETTLE(h);
+        h->aa_fi_valid = false;
         CK(h, launch_unpack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, h->inv_scale, src, h->g.nx,
                             h->g.ny, h->g.nz, h->nxp, inc_view(h), h->stream));
         h->launches += 1;
@@ -1523,6 +1623,7 @@ int32_t lbem_probe(lbem_handle h, const int32_t *xyz, int32_t n, float *out)
     int *d_xyz = (int *)h->scratch;
     float *d_out = (float *)(h->scratch) + 3 * LBEM_PROBE_MAX;
     CK(h, cudaMemcpyAsync(d_xyz, xyz, (size_t)n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    AA_SETTLE(h);
     CK(h, launch_probe(h->g.mode, h->g.storage, h->f[h->cur], h->scale, h->P, h->g.ny, h->nxp, d_xyz, n,
                        inc_view(h), d_out, h->stream));
     h->launches += 1;
@@ -1537,6 +1638,7 @@ int32_t lbem_fields(lbem_handle h, float *E, float *H, int32_t on_device)
     for (int comp = 0; comp < 6; ++comp) {
         float *dst = (comp < 3 ? E : H) + (size_t)(comp % 3) * h->ncell;
         float *out = on_device ? dst : h->stage;
+        AA_SETTLE(h);
         CK(h, launch_fields(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->mu_on ? h->inv_mu : nullptr, h->scale, h->P,
                             h->g.nx, h->g.ny, h->g.nz, h->nxp, inc_view(h), comp, out, h->stream));
         h->launches += 1;
@@ -1572,6 +1674,7 @@ int32_t lbem_energy(lbem_handle h, double *out)
     double *d_out = h->scratch;
     double *part = h->scratch + 8;
     int l = 0;
+    AA_SETTLE(h);
     CK(h, launch_energy(h->g.mode, h->g.storage, h->f[h->cur], h->inv_eps, h->mu_on ? h->inv_mu : nullptr, h->scale, h->P, h->g.nx,
                         h->g.ny, h->g.nz, h->nxp, inc_view(h), part, (int)(h->scratch_doubles - 8),
                         d_out, h->stream, &l));
@@ -1620,6 +1723,7 @@ int32_t lbem_save_state(lbem_handle h, void *buf, size_t bytes)
     char *p = (char *)buf;
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
+    AA_SETTLE(h);
     CK(h, cudaMemcpyAsync(p, h->f[h->cur], hd.pop_bytes, cudaMemcpyDeviceToHost, h->stream));
     p += hd.pop_bytes;
     for (int k = 0; k < 2; ++k) {  // incident line at t and t+1
@@ -1646,6 +1750,10 @@ int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
         return fail(h, LBEM_ERR_ARG, "snapshot does not match this grid");
     h->adj_valid = false;
     const char *p = (const char *)buf + sizeof hd;
+    if (h->aa) {  // the snapshot replaces the whole state, in the canonical layout
+        h->aa_phase = 0;
+        h->aa_fi_valid = false;
+    }
     CK(h, cudaMemcpyAsync(h->f[h->cur], p, hd.pop_bytes, cudaMemcpyHostToDevice, h->stream));
     p += hd.pop_bytes;
     for (int k = 0; k < 2; ++k) {  // incident line at t and t+1 of the snapshot
@@ -1676,8 +1784,11 @@ int32_t lbem_set_storage_scale(lbem_handle h, float scale)
         IncView none;
         std::memset(&none, 0, sizeof none);
         for (int q = 0; q < h->Q; ++q) {
+            AA_SETTLE(h);
             CK(h, launch_pack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, ratio, h->stage, h->g.nx, h->g.ny,
                               h->g.nz, h->nxp, none, h->stream));
+            AA_SETTLE(h);
+            h->aa_fi_valid = false;
             CK(h, launch_unpack(h->g.mode, h->g.storage, h->f[h->cur], h->P, q, 1.0f, h->stage, h->g.nx, h->g.ny,
                                 h->g.nz, h->nxp, none, h->stream));
             h->launches += 2;
@@ -1772,6 +1883,7 @@ int32_t lbem_forward_checkpointed(lbem_handle h, int64_t n_steps, int32_t K, voi
     if (h->g.storage != LBEM_F32) return fail(h, LBEM_ERR_ARG, "the adjoint needs FP32 storage");
     if (h->mu_on) return fail(h, LBEM_ERR_ARG, "the adjoint supports mu_r = 1 only");
     if (h->analytic) return fail(h, LBEM_ERR_ARG, "the adjoint needs the incident-line source");
+    if (h->aa) return fail(h, LBEM_ERR_ARG, "the adjoint needs two population buffers (not in-place streaming)");
     if (!h->has_wave) return fail(h, LBEM_ERR_STATE, "inject a plane wave first");
     if (h->t != 0) return fail(h, LBEM_ERR_STATE, "the checkpointed run must start at t = 0 (got t = %lld)",
                                (long long)h->t);
@@ -1823,6 +1935,7 @@ int32_t lbem_adjoint(lbem_handle h, const double *theta, const double *phi, cons
                      int32_t n_ang, float *grad_out, int32_t grad_on_device, double *J_out)
 {
     if (!h) return fail(nullptr, LBEM_ERR_ARG, "NULL handle");
+    if (h->aa) return fail(h, LBEM_ERR_ARG, "the adjoint needs two population buffers (not in-place streaming)");
     if (!h->adj_valid)
         return fail(h, LBEM_ERR_STATE, "no checkpointed forward run for the current permittivity and window");
     if (n_ang < 1 || n_ang > kAngleBatch || !theta || !weights || !grad_out)

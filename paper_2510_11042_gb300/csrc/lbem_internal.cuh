@@ -283,6 +283,32 @@ cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s
 cudaError_t launch_step2(int mode, int storage, int variant, const StepArgs &s1, const StepArgs &s2,
                          cudaStream_t s, int share = 1);
 bool step2_worthwhile(int mode, int storage, int variant, int nx, int ny, int nz, int share = 1);
+
+// In-place streaming on one population buffer (aa.cu).  Face buffers of
+// direction i = 1..6 on axis (i - 1) / 2 ([NC][fplane[axis]] storage
+// elements, face cell k: the other two coordinates, the lower one fastest):
+// fi[i] holds P_i of the cells whose upstream neighbour x - c_i is outside,
+// fo[i] P_i of the cells whose downstream neighbour x + c_i is outside; NULL
+// along 1-cell axes.
+struct AaArgs {
+    void *fi[7];
+    void *fo[7];
+    long long fplane[3];
+};
+// One step: kind 0 (push) from the canonical state, reading fin_q (slot i)
+// and writing through fout_q aimed at slot opp(i); kind 1 (in place) from the
+// streamed state, reading through fin_q aimed at slot opp(i) and writing
+// fout_q (slot i).  fin_q and fout_q address the same buffer.  variant as
+// for launch_step2 (0 plain, 1 mu_r map, 2 closed-form source).
+cudaError_t launch_aa_step(int mode, int storage, int variant, int kind, const StepArgs &a, const AaArgs &g,
+                           cudaStream_t s);
+// Fill fi from a canonical state (after any change to the state other than
+// an in-place step).
+cudaError_t launch_aa_fill(int mode, int storage, const void *buf, long long P, int nx, int ny, int nz, int nxp,
+                           const AaArgs &g, cudaStream_t s);
+// Turn the streamed state (after a push step) into the canonical one.
+cudaError_t launch_aa_canonical(int mode, int storage, void *buf, long long P, int nx, int ny, int nz, int nxp,
+                                const AaArgs &g, cudaStream_t s);
 // The step kernel with a per-cell mu_r (a.inv_mu), Eq. 2's h_0 = (mu_r - 1) H
 cudaError_t launch_step_mu(int mode, int storage, const StepArgs &a, cudaStream_t s);
 // The step kernel with the analytic plane-wave source (a.tfsf == 2; reads a.inv_mu)

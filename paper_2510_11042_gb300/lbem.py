@@ -29,6 +29,9 @@ LBEM_SOURCE_LINE = 0
 LBEM_SOURCE_ANALYTIC = 1
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 MODE = {"ez": 0, "hz": 1, "3d": 2}
+LBEM_STREAM_TWO_BUFFERS = 0
+LBEM_STREAM_IN_PLACE = 1
+STREAMING = {"two_buffers": LBEM_STREAM_TWO_BUFFERS, "in_place": LBEM_STREAM_IN_PLACE}
 
 
 class LbemError(RuntimeError):
@@ -40,7 +43,7 @@ class LbemError(RuntimeError):
 class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("absorber_width", ctypes.c_int32), ("sigma_max", ctypes.c_double),
-                ("storage", ctypes.c_int32), ("mode", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("mode", ctypes.c_int32), ("streaming", ctypes.c_int32)]
 
 
 class PlaneWaveDesc(ctypes.Structure):
@@ -154,8 +157,9 @@ def _ptr(x):
     return x.ctypes.data, 0
 
 
-def grid_desc(nx, ny, nz, mode="3d", storage="f32", absorber_width=0, sigma_max=0.3) -> GridDesc:
-    return GridDesc(nx, ny, nz, absorber_width, sigma_max, STORAGE[storage], MODE[mode])
+def grid_desc(nx, ny, nz, mode="3d", storage="f32", absorber_width=0, sigma_max=0.3,
+              streaming="two_buffers") -> GridDesc:
+    return GridDesc(nx, ny, nz, absorber_width, sigma_max, STORAGE[storage], MODE[mode], STREAMING[streaming])
 
 
 def plane_wave_desc(wave) -> PlaneWaveDesc:
@@ -538,7 +542,7 @@ class Solver:
     """One lattice on the current CUDA device, workspace owned by torch."""
 
     def __init__(self, shape, eps, mode="3d", storage="f32", absorber_width=0, sigma_max=0.3,
-                 device=None):
+                 device=None, streaming="two_buffers"):
         import torch
         self.torch = torch
         nx, ny, nz = shape
@@ -546,7 +550,8 @@ class Solver:
         self.mode = mode
         self.storage = storage
         self.Q = n_planes(mode)
-        self.grid = grid_desc(nx, ny, nz, mode, storage, absorber_width, sigma_max)
+        self.streaming = streaming
+        self.grid = grid_desc(nx, ny, nz, mode, storage, absorber_width, sigma_max, streaming)
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
         with torch.cuda.device(dev):
@@ -601,9 +606,10 @@ class Solver:
         return lbem_far_field(self.h, theta, phi, with_amplitudes)
 
     def set_step_fusion(self, steps_per_pass):
-        """2 (default): two steps per pass over the populations where supported
-        and worthwhile (3D grids without a mu_r map or closed-form source); 1:
-        single steps."""
+        """2 (default): two steps per pass over the populations where they pay
+        (grids of any mode and storage, with or without a mu_r map, that fill
+        the GPU; not the closed-form source or in-place streaming); 1: single
+        steps."""
         lbem_set_step_fusion(self.h, steps_per_pass)
 
     def step_fusion(self):

@@ -67,11 +67,11 @@ def oracle_faces(phasor_grid, mode, lo, hi):
     return faces
 
 
-def gpu_solver(problem, storage="f32", init=None, steps=None, dft=True):
+def gpu_solver(problem, storage="f32", init=None, steps=None, dft=True, streaming="two_buffers"):
     """Build a library solver for a workloads.Problem and advance it."""
     from paper_2510_11042_gb300 import lbem
     s = lbem.Solver(problem.shape, problem.eps, problem.mode, storage, problem.absorber_width,
-                    problem.sigma_max)
+                    problem.sigma_max, streaming=streaming)
     if getattr(problem, "mu", None) is not None:
         s.set_permeability(problem.mu)
     if init is not None:

@@ -42,6 +42,27 @@ def test_workspace_bytes_matches_layout():
     assert lbem.lbem_workspace_bytes(g2) > 2 * 21 * 1024 * 1024 * 4
 
 
+def test_in_place_streaming_halves_the_population_memory():
+    """One population buffer plus, per axis, FI and FO face buffers of both
+    directions (4 x NC values per face cell): at 384^3 FP32 that is 9.51 GB
+    less, less 4 x 6 x 3 x 384^2 x 4 B = 42.5 MB of faces."""
+    pop = 42 * 384 ** 3 * 4
+    for storage, elem in (("f32", 4), ("f16", 2)):
+        two = lbem.lbem_workspace_bytes(lbem.grid_desc(384, 384, 384, "3d", storage, 16))
+        one = lbem.lbem_workspace_bytes(lbem.grid_desc(384, 384, 384, "3d", storage, 16, streaming="in_place"))
+        faces = 4 * 6 * 3 * 384 ** 2 * elem
+        assert abs((two - one) - (pop * elem // 4 - faces)) < 4096, (two, one)
+    # 2D: faces along x and y only (the 1-cell z axis needs none)
+    two = lbem.lbem_workspace_bytes(lbem.grid_desc(1024, 1024, 1, "ez", "f32", 20))
+    one = lbem.lbem_workspace_bytes(lbem.grid_desc(1024, 1024, 1, "ez", "f32", 20, streaming="in_place"))
+    assert abs((two - one) - (21 * 1024 * 1024 * 4 - 4 * 3 * 2 * 1024 * 4)) < 4096
+    g = lbem.grid_desc(8, 8, 1, "ez", "f32", 0)
+    g.streaming = 2
+    with pytest.raises(lbem.LbemError) as ei:
+        lbem.lbem_workspace_bytes(g)
+    assert ei.value.code == lbem.LBEM_ERR_ARG and "streaming" in str(ei.value)
+
+
 @pytest.mark.parametrize("args,needle", [
     ((8, 8, 2, "ez", "f32", 0), "nz == 1"),
     ((8, 8, 1, "3d", "f32", 0), "nz >= 2"),
