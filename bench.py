@@ -293,6 +293,7 @@ def run_gpu(args, rank, world, local_rank):
     probe_2d = None if (args.no_batch or world > 1) else run_probe_2d(dev)
     variants_3d = None if (args.no_batch or world > 1) else run_variants_3d(dev)
     in_place = None if (args.no_batch or world > 1) else run_in_place(dev, n=args.size)
+    cyl_1024 = None if (args.no_batch or world > 1) else run_cylinder_1024(dev)
     batched = None if (args.no_batch or world > 1) else run_batched(dev)
     adjoint = None if (args.no_adjoint or world > 1) else run_adjoint(dev)
     secondary = {}
@@ -369,6 +370,8 @@ def run_gpu(args, rank, world, local_rank):
         line["kernel_variants_3d"] = variants_3d
     if in_place:
         line["in_place_streaming"] = in_place
+    if cyl_1024:
+        line["cylinder_1024"] = cyl_1024
     if batched:
         line["batched"] = batched
     if adjoint:
@@ -519,6 +522,49 @@ def run_probe_2d(dev, n=4096, updates=60):
             out[st]["dram_traffic_per_launch"] = traffic
             out[st]["dram_traffic_gbs"] = round(gbs_t, 1)
             out[st]["dram_traffic_frac"] = round(gbs_t / hbm, 4)
+    return out
+
+
+# ------------------------------------------------------------------ the 1024^2 cylinder workload
+def run_cylinder_1024(dev, updates=120):
+    """Step throughput on the cylinder workload itself (1024^2, a = 31.83,
+    eps_r = 2.25, W = 20, TM and TE) over one DFT window of 120 updates, with
+    the pass lbem_step takes (single steps: two 1024^2 buffers stay in L2).
+    The byte model's fraction is labelled L2-assisted where the working set is
+    under three times the L2 size."""
+    import torch
+    from paper_2510_11042_gb300 import lbem
+    hbm, _ = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    l2 = int(getattr(props, "L2_cache_size", 0)) or None
+    out = {"workload": "cylinder 1024^2, a 31.83, eps_r 2.25, lambda 40, W 20", "updates_timed": updates,
+           "l2_bytes": l2}
+    for mode in ("ez", "hz"):
+        p = W.cylinder_problem(n=1024, x=5.0, wavelength=40.0, eps_in=2.25, w=20, mode=mode, periods=40)
+        cells = int(np.prod(p.shape))
+        for st in ("f32", "f16", "bf16"):
+            s = lbem.Solver(p.shape, p.eps, mode, st, p.absorber_width, p.sigma_max, device=dev)
+            s.inject(p.wave)
+            s.step(10)
+            s.set_dft_window(s.time + 1, 1)
+            torch.cuda.synchronize(dev)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(s.stream)
+            s.step(updates)
+            ev[1].record(s.stream)
+            torch.cuda.synchronize(dev)
+            ms = ev[0].elapsed_time(ev[1]) / updates
+            bc = b_cell(mode, st)
+            gbs = bc * cells / (ms / 1e3) / 1e9
+            working = (2 * (42 if mode == "3d" else 21) * (4 if st == "f32" else 2) + 4) * cells
+            out[f"{mode}_{st}"] = {"kernel_ms": round(ms, 4), "mlups": round(cells / (ms / 1e3) / 1e6, 1),
+                                   "bytes_per_cell": bc, "achieved_gbs": round(gbs, 1),
+                                   "hbm_frac": round(gbs / hbm, 4), "steps_per_pass": s.step_fusion(),
+                                   "working_set_mb": round(working / 1e6, 1),
+                                   "label": ("L2-assisted" if l2 and working < 3 * l2 else "HBM")}
+            s.close()
+            del s
+            torch.cuda.empty_cache()
     return out
 
 
@@ -832,8 +878,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-updates", type=float, default=2)
     ap.add_argument("--section", default="all",
-                    choices=["all", "adjoint_probe", "probe_2d", "variants_3d", "in_place"],
-                    help="adjoint_probe / probe_2d / variants_3d / in_place: only that measurement (profiling)")
+                    choices=["all", "adjoint_probe", "probe_2d", "variants_3d", "in_place", "cylinder_1024"],
+                    help="adjoint_probe / probe_2d / variants_3d / in_place / cylinder_1024: only that "
+                         "measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -843,7 +890,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.section in ("adjoint_probe", "probe_2d", "variants_3d", "in_place"):
+    if args.section in ("adjoint_probe", "probe_2d", "variants_3d", "in_place", "cylinder_1024"):
         import torch
         from paper_2510_11042_gb300 import build as lib_build
         lib_build.build()
@@ -852,6 +899,8 @@ def main():
             out = run_variants_3d(dev, n=args.size)
         elif args.section == "in_place":
             out = run_in_place(dev, n=args.size)
+        elif args.section == "cylinder_1024":
+            out = run_cylinder_1024(dev)
         else:
             out = {"adjoint_probe": _adjoint_probe_3d, "probe_2d": run_probe_2d}[args.section](dev)
         print(json.dumps(out), flush=True)

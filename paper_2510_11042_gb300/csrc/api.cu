@@ -36,7 +36,7 @@ struct lbem_ctx {
     bool mu_on = false;
     bool analytic = false;      // the plane wave is the closed-form source, not the line
     PlaneWaveA pw;
-    float *line[3] = {nullptr, nullptr, nullptr};  // incident line at t, t+1, t+2 (mod 3)
+    float *line[kLineBufs] = {};  // incident line, line(t) in line[t mod kLineBufs]
     int n_line_max = 0;
     double *dft = nullptr;
     size_t dft_doubles_max = 0;
@@ -158,7 +158,7 @@ static int aa_settle(lbem_ctx *h)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t f0, f1, inv_eps, inv_mu, pw_tab, line0, line1, line2, dft, line_dft, scratch, ff32, stage, flag, total;
+    size_t f0, f1, inv_eps, inv_mu, pw_tab, line[kLineBufs], dft, line_dft, scratch, ff32, stage, flag, total;
     size_t x32_cap, tab32_cap;  // float2 capacities of the 3D FP32 far field (0 in 2D)
     size_t xstage, xstage_floats;  // staged face DFT fields
     size_t aa_faces;               // in-place streaming: FI and FO of the six directions
@@ -224,9 +224,7 @@ static Layout make_layout(const lbem_grid_desc *g)
     L.inv_eps = take((size_t)L.P * 4);
     L.inv_mu = take((size_t)L.P * 4);
     L.pw_tab = take((size_t)(g->nx + g->ny + g->nz) * 12);
-    L.line0 = take((size_t)L.Q * L.n_line_max * 4);
-    L.line1 = take((size_t)L.Q * L.n_line_max * 4);
-    L.line2 = take((size_t)L.Q * L.n_line_max * 4);
+    for (int k = 0; k < kLineBufs; ++k) L.line[k] = take((size_t)L.Q * L.n_line_max * 4);
     L.dft = take(L.dft_doubles_max * 8);
     L.line_dft = take((size_t)L.n_line_max * 6 * 8);
     L.scratch = take(L.scratch_doubles * 8);
@@ -286,7 +284,7 @@ static void source_fields(const lbem_ctx *h, int64_t t, float E[3], float H[3])
     }
 }
 
-static float *line_at(lbem_ctx *h, int64_t t) { return h->line[(int)(((t % 3) + 3) % 3)]; }
+static float *line_at(lbem_ctx *h, int64_t t) { return h->line[(int)(((t % kLineBufs) + kLineBufs) % kLineBufs)]; }
 
 static IncView inc_view(lbem_ctx *h)
 {
@@ -468,9 +466,7 @@ int32_t lbem_create(const lbem_grid_desc *grid, int32_t velocity_set, const floa
     h->inv_mu = (float *)(h->ws + L.inv_mu);
     h->pw_ph = (float2 *)(h->ws + L.pw_tab);
     h->pw_d = (float *)(h->pw_ph + (grid->nx + grid->ny + grid->nz));
-    h->line[0] = (float *)(h->ws + L.line0);
-    h->line[1] = (float *)(h->ws + L.line1);
-    h->line[2] = (float *)(h->ws + L.line2);
+    for (int k = 0; k < kLineBufs; ++k) h->line[k] = (float *)(h->ws + L.line[k]);
     h->n_line_max = L.n_line_max;
     h->dft = (double *)(h->ws + L.dft);
     h->dft_doubles_max = L.dft_doubles_max;
@@ -940,8 +936,13 @@ static int step_loop(lbem_ctx *h, int64_t n)
     StepArgs a;
     fill_common_args(h, a);
     const bool pairs = two_step_passes(h);
-    StepArgs a2;
-    if (pairs) fill_common_args(h, a2);
+    StepArgs a2, la[2];
+    if (pairs) {
+        fill_common_args(h, a2);
+        fill_common_args(h, la[0]);
+        fill_common_args(h, la[1]);
+    }
+    bool line_ready = false;  // the previous pass advanced the incident line for this one
     for (int64_t k = 0; k < n;) {
         if (pairs && n - k >= 2) {
             // two steps in one pass: level n from f[cur], level n+2 into f[cur ^ 1]
@@ -954,12 +955,21 @@ static int step_loop(lbem_ctx *h, int64_t n)
             const int cnt0 = h->xs_cnt;
             stage_slot(h, a, h->xs_allmask);
             stage_slot(h, a2, h->xs_allmask);
-            cudaError_t e = launch_step2(h->g.mode, h->g.storage, step_variant(h), a, a2, h->stream, h->share);
+            // a 2D pass that another pass of this call follows advances the
+            // incident line for it (the line work of steps t+2 and t+3)
+            const bool ahead = a.line_on && h->g.mode != 2 && n - k >= 4;
+            if (ahead) {
+                step_args_at(h, la[0], h->t + 2, h->cur, h->cur ^ 1);
+                step_args_at(h, la[1], h->t + 3, h->cur ^ 1, h->cur ^ 1);
+            }
+            cudaError_t e = launch_step2(h->g.mode, h->g.storage, step_variant(h), a, a2, h->stream, h->share,
+                                         ahead ? la : nullptr, line_ready);
             if (e != cudaSuccess) {
                 h->xs_cnt = cnt0;   // the claimed slots hold nothing
                 return cuda_fail(h, e, "two-step kernel launch");
             }
-            h->launches += a.line_on ? 2 : 1;
+            h->launches += (a.line_on && !line_ready) ? 2 : 1;
+            line_ready = ahead;
             h->cur ^= 1;
             h->t += 2;
             k += 2;
@@ -971,6 +981,7 @@ static int step_loop(lbem_ctx *h, int64_t n)
                 const int rc = flush_x_stage(h, false);
                 if (rc != LBEM_OK) return rc;
             }
+            line_ready = false;
             const int kind = h->aa_phase;  // in-place streaming: 0 push, 1 in place
             if (h->aa && kind == 0 && !h->aa_fi_valid) {
                 CK(h, launch_aa_fill(h->g.mode, h->g.storage, h->f[0], h->P, h->g.nx, h->g.ny, h->g.nz, h->nxp,
@@ -1171,7 +1182,7 @@ static int batch_chunk(lbem_batch_ctx *b, std::vector<int64_t> &left, int64_t ch
         items += P.nitems;
         P.f_base[0] = (const char *)h->f[0];
         P.f_base[1] = (const char *)h->f[1];
-        for (int k = 0; k < 3; ++k) P.line[k] = h->line[k];
+        for (int k = 0; k < kLineBufs; ++k) P.line[k] = h->line[k];
         P.plane_bytes = (long long)h->P * (long long)h->elem;
         P.t0 = h->t;
         P.steps = std::min<int64_t>(left[i], chunk);
@@ -1757,7 +1768,7 @@ int32_t lbem_load_state(lbem_handle h, const void *buf, size_t bytes)
     CK(h, cudaMemcpyAsync(h->f[h->cur], p, hd.pop_bytes, cudaMemcpyHostToDevice, h->stream));
     p += hd.pop_bytes;
     for (int k = 0; k < 2; ++k) {  // incident line at t and t+1 of the snapshot
-        CK(h, cudaMemcpyAsync(h->line[(int)((hd.t + k) % 3)], p, hd.line_bytes, cudaMemcpyHostToDevice,
+        CK(h, cudaMemcpyAsync(line_at(h, hd.t + k), p, hd.line_bytes, cudaMemcpyHostToDevice,
                               h->stream));
         p += hd.line_bytes;
     }
@@ -1918,9 +1929,11 @@ int32_t lbem_forward_checkpointed(lbem_handle h, int64_t n_steps, int32_t K, voi
     for (int seg = 0; seg < L.nseg; ++seg) {
         char *ck = h->adj_ws + L.ck0 + (size_t)seg * L.ck_stride;
         CK(h, cudaMemcpyAsync(ck, h->f[h->cur], pop, cudaMemcpyDeviceToDevice, h->stream));
+        // the replay keeps line(t) in buffer t mod 3
+        const int64_t t0 = (int64_t)seg * K;
         for (int k = 0; k < 3; ++k)
-            CK(h, cudaMemcpyAsync(ck + L.ck_lines + k * align256(line), h->line[k], line,
-                                  cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, cudaMemcpyAsync(ck + L.ck_lines + (size_t)((t0 + k) % 3) * align256(line), line_at(h, t0 + k),
+                                  line, cudaMemcpyDeviceToDevice, h->stream));
         const int64_t len = std::min<int64_t>(K, n_steps - (int64_t)seg * K);
         const int rc = lbem_step(h, len);
         if (rc != LBEM_OK) return rc;

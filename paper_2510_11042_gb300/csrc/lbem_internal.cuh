@@ -13,6 +13,10 @@
 namespace lbem {
 
 constexpr int kMaxDevices = 64;  // per-device set-up caches
+// Buffers of the incident line: a two-step pass reads line(n+1) and line(n+2)
+// while its first block may already advance the line for the next pass,
+// reading line(n+3) and writing line(n+4) and line(n+5).
+constexpr int kLineBufs = 5;
 // Streaming multiprocessors and L2 bytes of the current device (queried once
 // per device; 0 if the query fails).
 int sm_count();
@@ -241,7 +245,7 @@ struct StepArgs {
 struct BatchProblem {
     StepArgs a;                 // static arguments; per-step fields filled in the kernel
     const char *f_base[2];      // the two population buffers
-    float *line[3];             // incident line buffers, line(t) in line[t % 3]
+    float *line[kLineBufs];     // incident line buffers, line(t) in line[t % kLineBufs]
     long long plane_bytes;
     long long t0, steps;        // time at the start of the run, steps to take
     int cur0;                   // buffer holding f*(t0)
@@ -280,8 +284,11 @@ cudaError_t launch_step(int mode, int storage, const StepArgs &a, cudaStream_t s
 // it updates the line for both steps (two launches in all).
 // share: how many grids step concurrently beside each other (the lanes of a
 // batched run), which the choice and the launch shape take into account.
+// ahead (2D, incident line on): the arguments of the next pass's two steps,
+// whose line work the first block does (line(n+4), line(n+5)); line_ready: the
+// previous pass did this pass's line work, so the one-block launch is left out.
 cudaError_t launch_step2(int mode, int storage, int variant, const StepArgs &s1, const StepArgs &s2,
-                         cudaStream_t s, int share = 1);
+                         cudaStream_t s, int share = 1, const StepArgs *ahead = nullptr, bool line_ready = false);
 bool step2_worthwhile(int mode, int storage, int variant, int nx, int ny, int nz, int share = 1);
 
 // In-place streaming on one population buffer (aa.cu).  Face buffers of

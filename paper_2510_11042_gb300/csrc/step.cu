@@ -171,8 +171,8 @@ __device__ void fill_step_args(StepArgs &sa, const BatchProblem &P, long long st
         sa.fout_q[q] = (void *)(P.f_base[in ^ 1] + q * P.plane_bytes);
     }
     if (!P.has_wave) return;
-    sa.line_n1 = P.line[(t + 1) % 3];
-    sa.line_out = P.line[(t + 2) % 3];
+    sa.line_n1 = P.line[(t + 1) % kLineBufs];
+    sa.line_out = P.line[(t + 2) % kLineBufs];
     // hard source at time t+2: E = E0 ramp(t) sin(w t) p, H = k x E
     const long long ts = t + 2;
     const double tr = (double)ts;
