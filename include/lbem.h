@@ -102,7 +102,8 @@ typedef struct {
  *    grids fit) updated in place by alternating a step that pushes each
  *    post-collision population into its downstream neighbour's opposite slot
  *    and a step that reads and writes only the cell's own slots (the "AA"
- *    pattern), with two thin face buffers per axis for the clamped faces.
+ *    pattern), with thin face buffers (four per axis longer than one cell) for
+ *    the clamped faces of Eq. 4.
  *    Single steps only.  The state is in its ordinary layout after an even
  *    number of steps; calls that read or set populations or fields after an
  *    odd number first rearrange it (one pass over the populations).
