@@ -241,7 +241,7 @@ static Layout make_layout(const lbem_grid_desc *g)
         L.tab32_cap = (size_t)(g->nx + g->ny + g->nz) * kAngleBatch;
     }
     L.ff32 = take((L.x32_cap + L.tab32_cap) * 8);
-    // kXStage steps of face fields; the faces of any NTFF box are bounded by
+    // two banks of kXBank steps of face fields; the faces of any NTFF box are bounded by
     // the grid's faces
     L.xstage_floats = g->mode == 2 ? (size_t)kXStage * NC * 2 *
                                          ((size_t)g->ny * g->nz + (size_t)g->nx * g->nz + (size_t)g->nx * g->ny)

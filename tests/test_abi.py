@@ -33,7 +33,7 @@ def test_workspace_bytes_matches_layout():
     n = lbem.lbem_workspace_bytes(g)
     pops = 2 * 42 * 384 * 384 * 384 * 4
     # besides the two population buffers (19.0 GB): three FP32 planes (1/eps_r,
-    # 1/mu_r, host staging; 0.68 GB), 16 steps of staged face fields (0.34 GB),
+    # 1/mu_r, host staging; 0.68 GB), two banks of 8 steps of staged face fields (0.34 GB),
     # the DFT accumulators, far-field tables and scratch (0.14 GB)
     assert pops < n < pops * 1.07
     g16 = lbem.grid_desc(384, 384, 384, "3d", "f16", 16)
